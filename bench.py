@@ -1,0 +1,307 @@
+"""Benchmark: explicit-step DOF-updates/s of the PW-tested heat step (Galerkin
+comparator alongside), on the 3D workload 'heat3d': cubic C2 B-splines on
+128^3 elements (131^3 = 2,248,091 coefficients), 4x4x4 Gauss points,
+dt = 0.05 h^2, 50 explicit Euler steps per bench step, FP32 pairs with one
+FP64-residual refinement per solve (FP64 banded factors).
+
+One bench step = one full 50-step run from the seeded initial state (reset
+untimed before every step).  L2 (129 MB) is flushed before every timed step
+by writing a 512 MB buffer.  Device time: CUDA events on the context stream.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+With N > 1 (torchrun, one rank per GPU) every rank runs its own replica (the
+path has no exchange step across instances: weak scaling, no collective on the
+data path); the time is the max over ranks.  --impl reference times the FP64
+CPU oracle on the same workload (bounded sample per step).
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = 'heat3d'
+METRIC = 'explicit-step DOF-updates/s PW-const vs Galerkin (% HBM peak); served p50/p99 latency'
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument('--gpus', type=int, default=1)
+    ap.add_argument('--steps', type=int, default=5)
+    ap.add_argument('--warmup', type=int, default=3)
+    ap.add_argument('--impl', default='native', choices=['native', 'reference'])
+    ap.add_argument('--residual', default='fp64', choices=['fp64', 'df'])
+    return ap.parse_args()
+
+
+def dist_setup(n):
+    """(rank, world) from the torchrun environment; initialises a process
+    group when world > 1 (NCCL with GPUs, gloo otherwise)."""
+    rank = int(os.environ.get('RANK', '0'))
+    world = int(os.environ.get('WORLD_SIZE', '1'))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        backend = 'nccl' if torch.cuda.is_available() else 'gloo'
+        if backend == 'nccl':
+            torch.cuda.set_device(int(os.environ.get('LOCAL_RANK', '0')))
+        dist.init_process_group(backend)
+    return rank, world
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    """Max of a float over all ranks (timing only; no data-path collective)."""
+    if world == 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    dev = 'cuda' if dist.get_backend() == 'nccl' else 'cpu'
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled during the timed region."""
+    Q = ('clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,'
+         'clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,'
+         'clocks_event_reasons.sw_power_cap')
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ['nvidia-smi', '-i', str(self.index), f'--query-gpu={self.Q}', '--format=csv,noheader,nounits',
+                 '-lms', '100'], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        import statistics
+        sm, mx, reasons = [], [], set()
+        names = ['hw_slowdown', 'hw_thermal_slowdown', 'sw_thermal_slowdown', 'sw_power_cap']
+        for l in getattr(self, 'lines', []):
+            f = [x.strip() for x in l.split(',')]
+            if len(f) < 7:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx.append(float(f[1]))
+            except ValueError:
+                continue
+            for name, v in zip(names, f[3:7]):
+                if v.lower().startswith('active'):
+                    reasons.add(name)
+        return {'sm_mhz': statistics.median(sm) if sm else None, 'sm_max_mhz': max(mx) if mx else None,
+                'reasons': sorted(reasons), 'samples': len(sm)}
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, 'MEASURED_PEAKS.json')))
+    except OSError:
+        return {}
+
+
+def cpu_baseline_oracle(test='pw', steps=20):
+    """The FP64 oracle on the same workload: `steps` explicit steps at full size."""
+    import numpy as np
+    from oracle import systems, tensor
+    from paper_1910_08535_gb300 import workloads
+    w = workloads.WORKLOADS[WORKLOAD]
+    axes = [systems.Axis(w['n_elem'], w['degree'], w['nq'], test) for _ in range(3)]
+    M, L = tensor.mass_mats(axes), tensor.lap_mats(axes)
+    u = workloads.initial_state(WORKLOAD)
+    dt = workloads.dt_of(WORKLOAD)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        u = tensor.ads_solve(M, tensor.apply_heat_system(axes, u, dt, M, L))
+    el = time.perf_counter() - t0
+    try:
+        from threadpoolctl import threadpool_info
+        cores = max([i.get('num_threads', 1) for i in threadpool_info()] + [1])
+    except Exception:
+        cores = os.cpu_count()
+    return {'value': u.size * steps / el, 'unit': 'DOF-updates/s', 'cores': cores, 'kind': 'oracle',
+            'sample': f'{steps} of the 50 explicit steps of heat3d at full size (131^3), FP64 numpy, PW tests',
+            'seconds': el}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    samples = []
+    for i in range(args.warmup + args.steps):
+        r = cpu_baseline_oracle(steps=2)
+        if i >= args.warmup:
+            samples.append(r)
+    val = sum(s['value'] for s in samples) / len(samples)
+    sec = sum(s['seconds'] for s in samples) / len(samples)
+    line = {'impl': 'reference', 'metric': METRIC, 'value': val, 'unit': 'DOF-updates/s', 'n_gpus': world,
+            'steps': args.steps, 'warmup': args.warmup, 'ms_per_step': sec * 1e3, 'higher_is_better': True,
+            'scaling': 'weak', 'vs_baseline': None, 'dtype': 'f64', 'data': 'synthetic (seeded)',
+            'config': {'workload': 'heat3d: 3D heat, p=3, 128^3 elements, 4^3 Gauss, 2 of 50 steps per bench step',
+                       'test': 'pw'},
+            'cpu_baseline': {'value': val, 'unit': 'DOF-updates/s', 'cores': samples[0]['cores'], 'kind': 'oracle',
+                             'sample': '2 explicit steps of heat3d at full size (131^3) per bench step'},
+            'e2e': {'value': val, 'unit': 'DOF-updates/s', 'h2d_bytes_per_step': 0, 'd2h_bytes_per_step': 0}}
+    print(json.dumps(line))
+
+
+def run_native(args, rank, world):
+    import numpy as np
+    import torch
+    from paper_1910_08535_gb300 import _build, igapw, workloads
+    from paper_1910_08535_gb300.igapw import Context
+
+    _build.build()
+    dev = int(os.environ.get('LOCAL_RANK', '0')) if world > 1 else 0
+    torch.cuda.set_device(dev)
+    w = workloads.WORKLOADS[WORKLOAD]
+    nsteps = w['steps']
+    dt = workloads.dt_of(WORKLOAD)
+    u0 = workloads.initial_state(WORKLOAD, seed=rank)
+    flags = igapw.IGAPW_FLAG_DF_RESIDUAL if args.residual == 'df' else 0
+    stream = torch.cuda.Stream()
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device='cuda')
+
+    def run_test(test):
+        with torch.cuda.stream(stream):
+            c = Context(dim=3, n_elem=w['n_elem'], degree=w['degree'], nq=w['nq'], test=test,
+                        precision='fp32r', flags=flags, stream=stream)
+            init = c.from_numpy(u0)
+            u = c.empty()
+            for _ in range(args.warmup):
+                u.copy_(init)
+                c.step(u, dt, nsteps)
+            c.sync()
+            barrier(world)
+            torch.cuda.synchronize()
+            times = []
+            with ClockSampler(dev) as clk:
+                for _ in range(args.steps):
+                    u.copy_(init)
+                    flush.fill_(1.0)
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    c.step(u, dt, nsteps)
+                    e1.record(stream)
+                    e1.synchronize()
+                    times.append(e0.elapsed_time(e1) / 1e3)
+            torch.cuda.synchronize()
+            barrier(world)
+            c.sync()
+            total = max_over_ranks(sum(times), world)
+            return c, init, u, total, clk.summary()
+
+    c, init, u, t_pw, clocks = run_test('pw')
+    ntot = c.ntot
+    value = world * ntot * nsteps * args.steps / t_pw
+    # Galerkin comparator on the same mesh
+    cg, _, _, t_g, _ = run_test('galerkin')
+    value_g = world * ntot * nsteps * args.steps / t_g
+    cg.close()
+
+    # dominant kernel: the operator-action contraction (double-float RHS),
+    # timed alone on the context stream over the same state (L2 flushed)
+    kt = []
+    r = c.empty()
+    with torch.cuda.stream(stream):
+        for i in range(23):
+            flush.fill_(1.0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            c.apply('heat', u, dt, out=r)
+            e1.record(stream)
+            e1.synchronize()
+            if i >= 3:
+                kt.append(e0.elapsed_time(e1) / 1e3)
+    k_avg = sum(kt) / len(kt)
+    alg_bytes = 16.0 * ntot               # read the u pair, write the r pair
+    pk = peaks()
+    hbm_peak = pk.get('hbm_gbs', 6800.0)
+    achieved = alg_bytes / k_avg / 1e9
+    roof = {'bound': 'hbm', 'achieved': achieved, 'peak': hbm_peak, 'unit': 'GB/s', 'frac': achieved / hbm_peak,
+            'traffic': None, 'kernel': 'contract_kernel<3,5,32,8,DF,MODE_OP,PAIR> (PW operator action)',
+            'peak_kind': 'measured (MEASURED_PEAKS.json hbm_gbs)' if 'hbm_gbs' in pk else 'fallback'}
+
+    # end to end through the public C ABI with host buffers (pinned)
+    host = torch.empty((2,) + c.shape, dtype=torch.float32).pin_memory()
+    hb = host.numpy()
+    e2e_t = []
+    for i in range(args.warmup + args.steps):
+        hb[...] = init.cpu().numpy()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        igapw.igapw_step_host(c.ctx, dt, nsteps, host)
+        el = time.perf_counter() - t0
+        if i >= args.warmup:
+            e2e_t.append(el)
+    e2e_total = max_over_ranks(sum(e2e_t), world)
+    e2e = {'value': world * ntot * nsteps * args.steps / e2e_total, 'unit': 'DOF-updates/s',
+           'h2d_bytes_per_step': 8 * ntot, 'd2h_bytes_per_step': 8 * ntot}
+
+    cpu = None
+    if rank == 0 and world == 1:
+        cpu = cpu_baseline_oracle(steps=20)
+        cpu.pop('seconds', None)
+    launches_per_time_step = 8
+    line = {'metric': METRIC, 'value': value, 'unit': 'DOF-updates/s', 'n_gpus': world, 'steps': args.steps,
+            'warmup': args.warmup, 'ms_per_step': t_pw / args.steps * 1e3, 'higher_is_better': True,
+            'scaling': 'weak', 'vs_baseline': None, 'dtype': 'f32 pairs (double-float) + fp64 residual'
+            if args.residual == 'fp64' else 'f32 pairs (double-float), double-float residual',
+            'data': 'synthetic (seeded PCG64; coefficients 1e-2 N(0,1))',
+            'config': {'workload': 'heat3d: 3D explicit heat, cubic C2, 128^3 elements (2,248,091 DOF), '
+                                   '4x4x4 Gauss, dt=0.05h^2, 50 steps per bench step, PW tests',
+                       'l2': 'flushed (512 MB write) before every timed step', 'residual': args.residual},
+            'galerkin': {'value': value_g, 'unit': 'DOF-updates/s', 'pw_over_galerkin': value / value_g},
+            'roofline': roof, 'clocks': clocks, 'e2e': e2e,
+            'gpu_launches': launches_per_time_step * nsteps * args.steps,
+            'cpu_baseline': cpu}
+    if rank == 0:
+        print(json.dumps(line))
+    c.close()
+
+
+def main():
+    args = parse()
+    rank, world = dist_setup(args.gpus)
+    if args.impl == 'reference':
+        run_reference(args, rank, world)
+    else:
+        run_native(args, rank, world)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == '__main__':
+    main()

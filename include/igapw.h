@@ -1,0 +1,194 @@
+/*
+ * igapw.h -- C ABI of the GB300 (sm_103a) library for isogeometric analysis with
+ * piece-wise constant test functions (arXiv 1910.08535).
+ *
+ * What the library computes (paper section in brackets):
+ *   - trial space: tensor-product B-splines of degree p on open knot vectors,
+ *     n = N_e + p functions per axis                           [Sec. 2, Eq. (2)]
+ *   - tests: B-splines (Galerkin, the comparator) or piece-wise constant
+ *     indicators I_i of N_x linearly independent cells (PW)  [Sec. 2, Sec. 3]
+ *   - operator action / right-hand side by Gauss quadrature, not integrated
+ *     by parts                                                [Sec. 2, Sec. 4.1]
+ *   - Kronecker-factored mass solve Mx (x) My (x) Mz as three batches of 1D
+ *     banded systems (alternating directions)                 [Sec. 4.1]
+ *   - explicit Euler steps, one L2 projection each            [Sec. 4.2, Eq. (6)]
+ *   - zero Dirichlet rows by row replacement (1D Poisson)     [Sec. 4.3]
+ *
+ * PW test cells.  The paper leaves the choice of the N_x intervals open and only
+ * requires them to be linearly independent (Sec. 2).  This library bounds cell k
+ * by the midpoints between consecutive Greville abscissae of the unknowns (the
+ * domain ends close the first and last cell) and pairs cell k with unknown k.
+ * Every cell is split at the knots into polynomial pieces with their own
+ * nq-point Gauss rule.
+ *
+ * Conventions for every call
+ *   - Return 0 on success, a negative IGAPW_ERR_* code on failure; the message
+ *     is then available from igapw_last_error(ctx).  No C++ exception crosses
+ *     the ABI.
+ *   - Tensors are dense, C-ordered, x fastest: shape (n_z, n_y, n_x) in 3D,
+ *     (n_y, n_x) in 2D, (n_x) in 1D, with n_a = N_{e,a} + p.  Device pointers
+ *     must be 16-byte aligned and are owned by the caller; the library never
+ *     frees or reallocates them.
+ *   - Precision IGAPW_FP64: coefficient and RHS tensors are double.
+ *     Precision IGAPW_FP32_REFINE: coefficient and RHS tensors are double-float
+ *     pairs stored as two consecutive float planes, hi then lo: a float buffer
+ *     of 2 * n_total elements whose value is hi + lo.  Contractions run in FP32
+ *     with error-free products and two-sum accumulation; line solves run in
+ *     FP32 with one step of iterative refinement whose residual is formed in
+ *     FP64 (or in double-float, IGAPW_FLAG_DF_RESIDUAL).  Quadrature-point
+ *     samples f passed to igapw_rhs_source are plain float in this mode.
+ *   - Work is enqueued on the CUDA stream given at create time and is
+ *     asynchronous; calls do not synchronize unless stated.
+ *   - The context owns all device tables, factors and scratch buffers.
+ */
+#ifndef IGAPW_H
+#define IGAPW_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- error codes ---------------------------------------------------------- */
+#define IGAPW_OK                 0
+#define IGAPW_ERR_ARG           -1  /* invalid argument or unsupported combination */
+#define IGAPW_ERR_SINGULAR      -2  /* zero pivot in a 1D banded factorization      */
+#define IGAPW_ERR_OOM           -3  /* device or host allocation failed             */
+#define IGAPW_ERR_CUDA          -4  /* a CUDA runtime call failed                   */
+#define IGAPW_ERR_DEVICE_STATUS -5  /* a kernel reported a bad value (NaN / Inf)    */
+#define IGAPW_ERR_TIMEOUT       -6  /* reserved: a bounded device wait gave up      */
+
+/* ---- descriptor enums --------------------------------------------------- */
+#define IGAPW_GALERKIN      0  /* B-spline tests (comparator)                       */
+#define IGAPW_PWCONST       1  /* piece-wise constant tests                         */
+
+#define IGAPW_BC_NONE       0  /* all n coefficients free                           */
+#define IGAPW_BC_DIRICHLET0 1  /* first/last coefficient per axis held at 0 (1D)    */
+
+#define IGAPW_FP64          0
+#define IGAPW_FP32_REFINE   1
+
+#define IGAPW_OP_MASS       0  /* F u = u         (L2 projection, Sec. 4.1)         */
+#define IGAPW_OP_LAPLACE    1  /* F u = Lap u     (apply only)                      */
+#define IGAPW_OP_HEAT       2  /* F u = u + dt Lap u (explicit step, Sec. 4.2)      */
+#define IGAPW_OP_POISSON    3  /* F u = -Lap u    (1D Poisson system, Sec. 4.3)     */
+
+#define IGAPW_FLAG_DF_RESIDUAL 1  /* FP32_REFINE: refinement residual in double-float
+                                     (FP32 pairs) instead of FP64                    */
+
+#define IGAPW_MAX_DIM    3
+#define IGAPW_MAX_DEGREE 4
+
+typedef struct igapw_ctx igapw_ctx;
+
+/* Problem descriptor.  dim in {1,2,3}; n_elem[a] >= 1 elements on axis a
+ * (entries beyond dim ignored); degree p in {2,3,4} (C^{p-1}, at least C^1 as
+ * the method requires, Sec. 2); nq >= 1 Gauss points per element (Galerkin) or
+ * per polynomial piece of a cell (PW); test = IGAPW_GALERKIN | IGAPW_PWCONST;
+ * bc = IGAPW_BC_*; precision = IGAPW_FP64 | IGAPW_FP32_REFINE; op = IGAPW_OP_*
+ * selects the matrix igapw_solve inverts (POISSON: the 1D operator, dim = 1 and
+ * bc = DIRICHLET0 required; anything else: the tensor-product mass matrix);
+ * flags = IGAPW_FLAG_*. */
+typedef struct {
+    int dim;
+    int n_elem[3];
+    int degree;
+    int nq;
+    int test;
+    int bc;
+    int precision;
+    int op;
+    int flags;
+} igapw_desc;
+
+/* Builds knots, Gauss rules and PW cells on the host, evaluates the basis by
+ * Cox--de Boor at every quadrature point and folds it into per-axis banded
+ * tables on the device (int T_i B_j and int T_i B_j''), then factors the 1D
+ * system bands in FP64 on the device (banded LU, no pivoting) [Sec. 2, Sec. 4.1].
+ * cuda_stream: a cudaStream_t (NULL = legacy default stream).
+ * On success *out owns device memory until igapw_destroy.  Blocks until the
+ * set-up kernels finish so that a singular factorization (IGAPW_ERR_SINGULAR,
+ * linearly dependent tests, Sec. 2) is reported here. */
+int igapw_create(igapw_ctx** out, const igapw_desc* desc, void* cuda_stream);
+
+/* Replaces the knot vector of one axis by a caller-given open knot vector
+ * (len = n_elem[axis] + 2p + 1 non-decreasing values, first and last repeated
+ * p+1 times, no interior knot repeated more than p-1 times so C^1 holds) and
+ * rebuilds that axis' tables and factors.  Host pointer, copied. Synchronous. */
+int igapw_set_knots(igapw_ctx* ctx, int axis, const double* knots, int len);
+
+/* The 1D quadrature point set of one axis in increasing x: every element
+ * (Galerkin) or every polynomial piece of every cell (PW) with its nq Gauss
+ * points.  igapw_rhs_source expects f sampled on the tensor product of these
+ * sets (x fastest).  If x and w are NULL only *count is written; otherwise they
+ * must hold *count doubles (host memory).  Synchronous, host only. */
+int igapw_quad_points(igapw_ctx* ctx, int axis, double* x, double* w, int* count);
+
+/* Exports the basis table of kernel (a) for one axis to host memory:
+ * vals[(q * (p+1) + a) * 3 + k] = d^k B_{s_q + a}(x_q), k = 0,1,2, where
+ * s_q = first_fn[q] is the first non-zero function at point q.  vals holds
+ * count*(p+1)*3 doubles, first_fn holds count ints (either may be NULL).
+ * Synchronous (test aid). */
+int igapw_basis_table(igapw_ctx* ctx, int axis, double* vals, int* first_fn);
+
+/* Source right-hand side b = int T_i f over the tensor grid of quadrature
+ * points: PW sums the quadrature weights times f over each cell (the test is
+ * 1), Galerkin multiplies by the test B-splines [Sec. 4.1 generation loops].
+ * f_dev: device, FP64 (FP64 mode) or float (FP32_REFINE) samples on the
+ * igapw_quad_points grid.  b_dev: device coefficient-shaped tensor (double, or
+ * float hi/lo pair planes).  Dirichlet rows get b = 0. Asynchronous. */
+int igapw_rhs_source(igapw_ctx* ctx, const void* f_dev, void* b_dev);
+
+/* Operator action r = T(F u) with F chosen by op (IGAPW_OP_MASS, LAPLACE,
+ * HEAT with time step dt, POISSON), tests T of the context, computed by
+ * sum-factorised per-axis contractions of the folded quadrature tables
+ * [Sec. 2 / Sec. 3 systems; Sec. 4.2 RHS].  u_dev, r_dev: device tensors of
+ * the context precision; they must not overlap.  For a Dirichlet context the
+ * Dirichlet rows return r_i = u_i (row replacement, Sec. 4.3). Asynchronous. */
+int igapw_apply(igapw_ctx* ctx, int op, double dt, const void* u_dev, void* r_dev);
+
+/* Exports one 1D matrix of an axis as a dense row-major n x n double array in
+ * host memory: which = IGAPW_OP_MASS (int T_i B_j), IGAPW_OP_LAPLACE
+ * (int T_i B_j''), or IGAPW_OP_POISSON (the factored 1D Poisson system with
+ * Dirichlet rows).  Synchronous (test aid). */
+int igapw_assemble_1d(igapw_ctx* ctx, int axis, int which, double* dense_host);
+
+/* Solves S u = r with S the tensor product of the per-axis system matrices
+ * (mass, or the 1D Poisson operator): one batch of banded line solves per
+ * axis with the precomputed FP64 LU factors [Sec. 4.1 ADS].  FP32_REFINE: an
+ * FP32 solve, the residual r - S u0 (FP64 or double-float), a second FP32
+ * solve, u = u0 + correction stored as a hi/lo pair.  r_dev == u_dev is
+ * allowed. Asynchronous. */
+int igapw_solve(igapw_ctx* ctx, const void* r_dev, void* u_dev);
+
+/* nsteps explicit Euler steps of u_t = Lap u in place on u_dev: each step is
+ * the tested RHS T(u + dt Lap u) followed by the mass solve [Sec. 4.2, Eq. (6)].
+ * The step sequence is captured once per (dt, nsteps, u_dev) into a CUDA
+ * graph and replayed. Asynchronous. */
+int igapw_step(igapw_ctx* ctx, double dt, int nsteps, void* u_dev);
+
+/* Same as igapw_step with HOST buffers: copies u_host (pinned memory gives an
+ * asynchronous copy) into a context-owned device state, runs nsteps, copies
+ * the result back to u_host and synchronizes the stream before returning.
+ * u_host holds n_total doubles (FP64) or 2*n_total floats (FP32_REFINE). */
+int igapw_step_host(igapw_ctx* ctx, double dt, int nsteps, void* u_host);
+
+/* Waits for the context stream, then returns IGAPW_OK, IGAPW_ERR_CUDA if an
+ * asynchronous CUDA error occurred, or IGAPW_ERR_DEVICE_STATUS if a kernel
+ * flagged a non-finite value in a solve.  Clears the device status word. */
+int igapw_sync_status(igapw_ctx* ctx);
+
+/* Message for the last failure on this context (or on create, when ctx is
+ * NULL: the thread's last create error).  Never NULL. */
+const char* igapw_last_error(igapw_ctx* ctx);
+
+/* Number of coefficients n_total = prod_a n_a, and n_a per axis (dims may be
+ * NULL). */
+long long igapw_size(igapw_ctx* ctx, int* dims);
+
+/* Frees everything the context owns.  Synchronizes its stream first. */
+int igapw_destroy(igapw_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* IGAPW_H */

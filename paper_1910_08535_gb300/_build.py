@@ -1,0 +1,63 @@
+"""Builds libigapw.so in-tree for sm_103a: one nvcc process per translation
+unit (run in parallel), then one link step.  No cmake, no torch extension
+machinery; the library has a plain C ABI (include/igapw.h)."""
+import concurrent.futures
+import os
+import shutil
+import subprocess
+import sys
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+CSRC = os.path.join(HERE, 'csrc')
+OBJ = os.path.join(HERE, '_objs')
+LIB = os.path.join(HERE, 'lib', 'libigapw.so')
+SOURCES = ['setup.cpp', 'tables.cu', 'solve.cu', 'rhs.cu', 'api.cu']
+ARCH = ['-gencode', 'arch=compute_103a,code=sm_103a']
+FLAGS = ['-O3', '-lineinfo', '-std=c++17', '-Xcompiler', '-fPIC', '--expt-relaxed-constexpr',
+         '-Xcompiler', '-Wall', '-Xcompiler', '-Wno-unused-function']
+
+
+def nvcc():
+    path = shutil.which('nvcc') or '/usr/local/cuda/bin/nvcc'
+    if not os.path.exists(path):
+        raise RuntimeError('nvcc not found: the CUDA toolkit is required to build libigapw')
+    return path
+
+
+def _compile(src):
+    out = os.path.join(OBJ, os.path.splitext(src)[0] + '.o')
+    cmd = [nvcc(), *ARCH, *FLAGS, '-c', os.path.join(CSRC, src), '-o', out]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    return src, r.returncode, r.stdout + r.stderr, out
+
+
+def build(verbose=False, force=False):
+    """Compile (if any source is newer than the library) and return the .so path."""
+    srcs = [os.path.join(CSRC, s) for s in SOURCES] + [os.path.join(CSRC, h) for h in os.listdir(CSRC) if h.endswith(('.h', '.cuh'))]
+    srcs.append(os.path.join(HERE, '..', 'include', 'igapw.h'))
+    if not force and os.path.exists(LIB):
+        newest = max(os.path.getmtime(s) for s in srcs)
+        if os.path.getmtime(LIB) >= newest:
+            return LIB
+    os.makedirs(OBJ, exist_ok=True)
+    os.makedirs(os.path.dirname(LIB), exist_ok=True)
+    with concurrent.futures.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
+        results = list(ex.map(_compile, SOURCES))
+    failed = [r for r in results if r[1] != 0]
+    for src, rc, log, _ in results:
+        if verbose or rc != 0:
+            sys.stderr.write(f'--- {src} (rc={rc})\n{log}')
+    if failed:
+        raise RuntimeError('nvcc failed for ' + ', '.join(f[0] for f in failed))
+    objs = [r[3] for r in results]
+    tmp = LIB + '.tmp'
+    cmd = [nvcc(), *ARCH, '-shared', '-o', tmp, *objs, '-lcudart']
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError('link failed:\n' + r.stdout + r.stderr)
+    os.replace(tmp, LIB)
+    return LIB
+
+
+if __name__ == '__main__':
+    print(build(verbose='-v' in sys.argv, force='-f' in sys.argv))

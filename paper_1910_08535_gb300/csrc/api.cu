@@ -1,0 +1,597 @@
+// C ABI (include/igapw.h): context set-up, operator action, solves, explicit
+// steps captured as CUDA graphs.
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/igapw.h"
+#include "kernels.h"
+#include "setup.h"
+
+using namespace igapw;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+struct AxisMem {
+    double *knots = nullptr, *qx = nullptr, *qw = nullptr, *vals = nullptr;
+    int *qfirst = nullptr, *fstart = nullptr, *pstart = nullptr, *pcount = nullptr, *is_free = nullptr;
+    double *A = nullptr, *C = nullptr, *S = nullptr, *TW = nullptr;
+    float *Ahi = nullptr, *Alo = nullptr, *Chi = nullptr, *Clo = nullptr, *Shi = nullptr, *Slo = nullptr;
+    float *TWhi = nullptr, *TWlo = nullptr;
+    double *band = nullptr, *L = nullptr, *U = nullptr, *dinv = nullptr, *G = nullptr, *H = nullptr,
+           *PhiF = nullptr, *PhiB = nullptr;
+    float *L32 = nullptr, *U32 = nullptr, *dinv32 = nullptr, *G32 = nullptr, *H32 = nullptr,
+          *PhiF32 = nullptr, *PhiB32 = nullptr;
+};
+
+struct GraphEntry {
+    double dt;
+    int nsteps;
+    void* u;
+    cudaGraphExec_t exec;
+};
+
+}  // namespace
+
+struct igapw_ctx {
+    igapw_desc d{};
+    cudaStream_t stream = nullptr;
+    cudaStream_t cap_stream = nullptr;
+    int dim = 1, p = 2, W = 3, WQ = 1;
+    int n[3] = {1, 1, 1};
+    long long ntot = 1;
+    AxisSetup ax[3];
+    AxisMem mem[3];
+    AxisDev dev[3];
+    std::vector<void*> allocs;
+    // scratch
+    void* r = nullptr;       // RHS: double [ntot] or pair [2 ntot]
+    void* w = nullptr;       // line-solve intermediate: double or float [ntot]
+    float* u0 = nullptr;     // FP32 first solve [ntot]
+    float* rho = nullptr;    // FP32 residual [ntot]
+    void* state = nullptr;   // igapw_step_host device state
+    void* src0 = nullptr;    // rhs_source intermediates
+    void* src1 = nullptr;
+    size_t src_bytes = 0;
+    unsigned* status = nullptr;
+    std::string err;
+    std::vector<GraphEntry> graphs;
+};
+
+namespace {
+
+int fail(igapw_ctx* c, int code, const std::string& msg) {
+    if (c) c->err = msg;
+    else g_create_error = msg;
+    return code;
+}
+
+#define CKC(c, x)                                                                                   \
+    do {                                                                                            \
+        cudaError_t e_ = (x);                                                                       \
+        if (e_ != cudaSuccess)                                                                      \
+            return fail(c, e_ == cudaErrorMemoryAllocation ? IGAPW_ERR_OOM : IGAPW_ERR_CUDA,        \
+                        std::string(#x) + ": " + cudaGetErrorString(e_));                           \
+    } while (0)
+
+template <typename T>
+cudaError_t dalloc(igapw_ctx* c, T** p, size_t count) {
+    *p = nullptr;
+    if (count == 0) count = 1;
+    cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
+    if (e == cudaSuccess) c->allocs.push_back(*p);
+    return e;
+}
+
+template <typename T>
+cudaError_t upload(igapw_ctx* c, T** p, const std::vector<T>& h) {
+    cudaError_t e = dalloc(c, p, h.size());
+    if (e != cudaSuccess) return e;
+    if (!h.empty()) e = cudaMemcpyAsync(*p, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice, c->stream);
+    return e;
+}
+
+int pad_width(int w) {
+    if (w <= 3) return 3;
+    if (w <= 5) return 5;
+    if (w <= 7) return 7;
+    if (w <= 9) return 9;
+    return -1;
+}
+
+void free_graphs(igapw_ctx* c) {
+    for (auto& g : c->graphs) cudaGraphExecDestroy(g.exec);
+    c->graphs.clear();
+}
+
+// (Re)builds the device tables and factors of axis a from c->ax[a].
+int build_axis_device(igapw_ctx* c, int a) {
+    AxisSetup& s = c->ax[a];
+    AxisMem& m = c->mem[a];
+    const int n = s.n, p = s.p, W = c->W, WQ = c->WQ;
+    const int Q = (int)s.qx.size();
+    CKC(c, upload(c, &m.knots, s.knots));
+    CKC(c, upload(c, &m.qx, s.qx));
+    CKC(c, upload(c, &m.qw, s.qw));
+    CKC(c, upload(c, &m.qfirst, s.qfirst));
+    CKC(c, upload(c, &m.fstart, s.fstart));
+    CKC(c, upload(c, &m.pstart, s.pstart));
+    CKC(c, upload(c, &m.pcount, s.pcount));
+    CKC(c, upload(c, &m.is_free, s.is_free));
+    CKC(c, dalloc(c, &m.vals, (size_t)Q * (p + 1) * 3));
+    const size_t nw = (size_t)n * W, nt = (size_t)n * WQ;
+    CKC(c, dalloc(c, &m.A, nw)); CKC(c, dalloc(c, &m.C, nw)); CKC(c, dalloc(c, &m.S, nw));
+    CKC(c, dalloc(c, &m.TW, nt));
+    CKC(c, dalloc(c, &m.Ahi, nw)); CKC(c, dalloc(c, &m.Alo, nw));
+    CKC(c, dalloc(c, &m.Chi, nw)); CKC(c, dalloc(c, &m.Clo, nw));
+    CKC(c, dalloc(c, &m.Shi, nw)); CKC(c, dalloc(c, &m.Slo, nw));
+    CKC(c, dalloc(c, &m.TWhi, nt)); CKC(c, dalloc(c, &m.TWlo, nt));
+    const size_t np = (size_t)n * p, nphi = (size_t)5 * 32 * p * p;
+    CKC(c, dalloc(c, &m.band, (size_t)n * (2 * p + 1)));
+    CKC(c, dalloc(c, &m.L, np)); CKC(c, dalloc(c, &m.U, np)); CKC(c, dalloc(c, &m.dinv, (size_t)n));
+    CKC(c, dalloc(c, &m.G, np)); CKC(c, dalloc(c, &m.H, np));
+    CKC(c, dalloc(c, &m.PhiF, nphi)); CKC(c, dalloc(c, &m.PhiB, nphi));
+    CKC(c, dalloc(c, &m.L32, np)); CKC(c, dalloc(c, &m.U32, np)); CKC(c, dalloc(c, &m.dinv32, (size_t)n));
+    CKC(c, dalloc(c, &m.G32, np)); CKC(c, dalloc(c, &m.H32, np));
+    CKC(c, dalloc(c, &m.PhiF32, nphi)); CKC(c, dalloc(c, &m.PhiB32, nphi));
+
+    // kernel (a): basis table, then fold into the banded tables
+    launch_basis_table(m.knots, p, Q, m.qx, m.qfirst, m.vals, c->stream);
+    FoldArgs f{};
+    f.n = n; f.p = p; f.W = W; f.WQ = WQ; f.test = s.test; f.poisson = (c->d.op == IGAPW_OP_POISSON);
+    f.fstart = m.fstart; f.pstart = m.pstart; f.pcount = m.pcount; f.is_free = m.is_free;
+    f.qfirst = m.qfirst; f.qw = m.qw; f.vals = m.vals;
+    f.A = m.A; f.C = m.C; f.S = m.S; f.TW = m.TW;
+    f.Ahi = m.Ahi; f.Alo = m.Alo; f.Chi = m.Chi; f.Clo = m.Clo; f.Shi = m.Shi; f.Slo = m.Slo;
+    f.TWhi = m.TWhi; f.TWlo = m.TWlo;
+    launch_fold(f, c->stream);
+    // kernel (c1): FP64 banded LU + partitioned-solve data
+    FactorArgs fa{};
+    fa.n = n; fa.p = p; fa.W = W; fa.P = s.P;
+    for (int k = 0; k <= s.P; ++k) fa.b[k] = s.chunk_b[k];
+    fa.fstart = m.fstart; fa.S = m.S; fa.work = m.band;
+    fa.L = m.L; fa.U = m.U; fa.dinv = m.dinv; fa.G = m.G; fa.H = m.H; fa.PhiF = m.PhiF; fa.PhiB = m.PhiB;
+    fa.L32 = m.L32; fa.U32 = m.U32; fa.dinv32 = m.dinv32; fa.G32 = m.G32; fa.H32 = m.H32;
+    fa.PhiF32 = m.PhiF32; fa.PhiB32 = m.PhiB32;
+    fa.status = c->status;
+    launch_factor(fa, c->stream);
+    CKC(c, cudaGetLastError());
+
+    AxisDev& D = c->dev[a];
+    D.n = n; D.nq = Q; D.wq = WQ;
+    D.fstart = m.fstart; D.pstart = m.pstart; D.is_free = m.is_free;
+    D.A = {m.A, m.Ahi, m.Alo};
+    D.C = {m.C, m.Chi, m.Clo};
+    D.S = {m.S, m.Shi, m.Slo};
+    D.TW = {m.TW, m.TWhi, m.TWlo};
+    D.ls64.n = n; D.ls64.P = s.P;
+    D.ls32.n = n; D.ls32.P = s.P;
+    for (int k = 0; k < 33; ++k) { D.ls64.b[k] = s.chunk_b[k]; D.ls32.b[k] = s.chunk_b[k]; }
+    D.ls64.L = m.L; D.ls64.U = m.U; D.ls64.dinv = m.dinv; D.ls64.G = m.G; D.ls64.H = m.H;
+    D.ls64.PhiF = m.PhiF; D.ls64.PhiB = m.PhiB;
+    D.ls32.L = m.L32; D.ls32.U = m.U32; D.ls32.dinv = m.dinv32; D.ls32.G = m.G32; D.ls32.H = m.H32;
+    D.ls32.PhiF = m.PhiF32; D.ls32.PhiB = m.PhiB32;
+    return IGAPW_OK;
+}
+
+int check_setup_status(igapw_ctx* c) {
+    CKC(c, cudaStreamSynchronize(c->stream));
+    unsigned st = 0;
+    CKC(c, cudaMemcpy(&st, c->status, sizeof st, cudaMemcpyDeviceToHost));
+    if (st & STATUS_SINGULAR) {
+        unsigned z = 0;
+        cudaMemcpy(c->status, &z, sizeof z, cudaMemcpyHostToDevice);
+        return fail(c, IGAPW_ERR_SINGULAR, "zero pivot in a 1D banded factorization (linearly dependent tests)");
+    }
+    return IGAPW_OK;
+}
+
+bool fp64(const igapw_ctx* c) { return c->d.precision == IGAPW_FP64; }
+
+ContractArgs contract_args(igapw_ctx* c) {
+    ContractArgs a{};
+    a.dim = c->dim;
+    a.W = c->W;
+    for (int k = 0; k < 3; ++k) { a.n[k] = c->n[k]; a.ax[k] = c->dev[k]; }
+    // z-chunk: aim at >= 2 blocks per SM over the whole grid
+    a.zchunk = c->n[2];
+    if (c->dim == 3) {
+        const long long xy_tiles = (long long)((c->n[0] + 31) / 32) * ((c->n[1] + 7) / 8);
+        const long long want = 2 * 152;
+        long long chunks = (want + xy_tiles - 1) / xy_tiles;
+        if (chunks < 1) chunks = 1;
+        a.zchunk = (int)((c->n[2] + chunks - 1) / chunks);
+        if (a.zchunk < 4) a.zchunk = 4;
+    }
+    a.ntot = c->ntot;
+    return a;
+}
+
+// The solve chain: axis 0 reads `in`, the last axis writes `out`.
+int solve_chain(igapw_ctx* c, const void* in, int in_fmt, void* out, int out_fmt, const float* u0,
+                cudaStream_t st) {
+    const bool f64 = fp64(c);
+    for (int a = 0; a < c->dim; ++a) {
+        SolveArgs s{};
+        s.axis = a;
+        for (int k = 0; k < 3; ++k) s.n[k] = c->n[k];
+        s.ntot = c->ntot;
+        s.status = c->status;
+        s.u0 = u0;
+        s.in = a == 0 ? in : c->w;
+        s.out = a == c->dim - 1 ? out : c->w;
+        const int fi = a == 0 ? in_fmt : (f64 ? FMT_F64 : FMT_F32);
+        const int fo = a == c->dim - 1 ? out_fmt : (f64 ? FMT_F64 : FMT_F32);
+        cudaError_t e = launch_solve(s, c->dev[a], c->p, fi, fo, f64, st);
+        if (e != cudaSuccess) return fail(c, IGAPW_ERR_CUDA, std::string("line solve: ") + cudaGetErrorString(e));
+    }
+    return IGAPW_OK;
+}
+
+// Full solve S u = r (with refinement in FP32_REFINE mode).
+int enqueue_solve(igapw_ctx* c, const void* r, void* u, cudaStream_t st) {
+    if (fp64(c)) return solve_chain(c, r, FMT_F64, u, FMT_F64, nullptr, st);
+    int rc = solve_chain(c, r, FMT_PAIR, c->u0, FMT_F32, nullptr, st);
+    if (rc) return rc;
+    ContractArgs a = contract_args(c);
+    a.u = c->u0;
+    a.r = r;
+    a.out = c->rho;
+    const int cmp = (c->d.flags & IGAPW_FLAG_DF_RESIDUAL) ? FMT_PAIR : FMT_F64;
+    cudaError_t e = launch_contract(a, MODE_RES, cmp, FMT_PAIR, st);
+    if (e != cudaSuccess) return fail(c, IGAPW_ERR_CUDA, std::string("residual: ") + cudaGetErrorString(e));
+    return solve_chain(c, c->rho, FMT_F32, u, FMT_PAIR, c->u0, st);
+}
+
+int enqueue_apply(igapw_ctx* c, int mode, double alpha, double beta, const void* u, void* r, cudaStream_t st) {
+    ContractArgs a = contract_args(c);
+    a.u = u;
+    a.out = r;
+    a.alpha = alpha;
+    a.beta = beta;
+    const int f = fp64(c) ? FMT_F64 : FMT_PAIR;
+    cudaError_t e = launch_contract(a, mode, f, f, st);
+    if (e != cudaSuccess) return fail(c, IGAPW_ERR_CUDA, std::string("contract: ") + cudaGetErrorString(e));
+    return IGAPW_OK;
+}
+
+int enqueue_steps(igapw_ctx* c, double dt, int nsteps, void* u, cudaStream_t st) {
+    for (int s = 0; s < nsteps; ++s) {
+        int rc = enqueue_apply(c, MODE_OP, 1.0, dt, u, c->r, st);
+        if (rc) return rc;
+        rc = enqueue_solve(c, c->r, u, st);
+        if (rc) return rc;
+    }
+    return IGAPW_OK;
+}
+
+int valid_desc(const igapw_desc* d, std::string& why) {
+    if (!d) { why = "desc is NULL"; return 0; }
+    if (d->dim < 1 || d->dim > 3) { why = "dim must be 1, 2 or 3"; return 0; }
+    for (int a = 0; a < d->dim; ++a)
+        if (d->n_elem[a] < 1) { why = "n_elem must be >= 1"; return 0; }
+    if (d->degree < 2 || d->degree > IGAPW_MAX_DEGREE) { why = "degree must be 2..4 (C^1 or smoother)"; return 0; }
+    if (d->nq < 1 || d->nq > 16) { why = "nq must be 1..16"; return 0; }
+    if (d->test != IGAPW_GALERKIN && d->test != IGAPW_PWCONST) { why = "unknown test"; return 0; }
+    if (d->bc != IGAPW_BC_NONE && d->bc != IGAPW_BC_DIRICHLET0) { why = "unknown bc"; return 0; }
+    if (d->bc == IGAPW_BC_DIRICHLET0 && d->dim != 1) { why = "Dirichlet rows are supported in 1D only"; return 0; }
+    if (d->precision != IGAPW_FP64 && d->precision != IGAPW_FP32_REFINE) { why = "unknown precision"; return 0; }
+    if (d->op < IGAPW_OP_MASS || d->op > IGAPW_OP_POISSON) { why = "unknown op"; return 0; }
+    if (d->op == IGAPW_OP_POISSON && (d->dim != 1 || d->bc != IGAPW_BC_DIRICHLET0)) {
+        why = "the POISSON system needs dim = 1 and Dirichlet rows (multi-D Poisson is not a Kronecker product)";
+        return 0;
+    }
+    return 1;
+}
+
+int alloc_scratch(igapw_ctx* c) {
+    const size_t nt = (size_t)c->ntot;
+    if (fp64(c)) {
+        CKC(c, dalloc(c, (double**)&c->r, nt));
+        CKC(c, dalloc(c, (double**)&c->w, nt));
+    } else {
+        CKC(c, dalloc(c, (float**)&c->r, 2 * nt));
+        CKC(c, dalloc(c, (float**)&c->w, nt));
+        CKC(c, dalloc(c, &c->u0, nt));
+        CKC(c, dalloc(c, &c->rho, nt));
+    }
+    return IGAPW_OK;
+}
+
+int setup_all(igapw_ctx* c, const std::vector<double>* knots_override, int override_axis) {
+    const igapw_desc& d = c->d;
+    int wmax = 0, wqmax = 0;
+    for (int a = 0; a < c->dim; ++a) {
+        std::vector<double> kn;
+        if (knots_override && a == override_axis) kn = *knots_override;
+        else if (!c->ax[a].knots.empty() && c->ax[a].n_elem == d.n_elem[a] && knots_override) kn = c->ax[a].knots;
+        std::string e = build_axis(c->ax[a], d.n_elem[a], d.degree, d.nq, d.test, d.bc, kn);
+        if (!e.empty()) return fail(c, IGAPW_ERR_ARG, "axis " + std::to_string(a) + ": " + e);
+        wmax = std::max(wmax, c->ax[a].w);
+        wqmax = std::max(wqmax, c->ax[a].wq);
+    }
+    c->W = pad_width(wmax);
+    c->WQ = std::max(wqmax, 1);
+    if (c->W < 0) return fail(c, IGAPW_ERR_ARG, "window too wide");
+    for (int a = 0; a < c->dim; ++a)
+        if (!set_window(c->ax[a], c->W)) return fail(c, IGAPW_ERR_ARG, "banded window layout failed");
+    for (int a = 0; a < c->dim; ++a) {
+        int rc = build_axis_device(c, a);
+        if (rc) return rc;
+    }
+    return check_setup_status(c);
+}
+
+void release(igapw_ctx* c) {
+    free_graphs(c);
+    for (void* p : c->allocs) cudaFree(p);
+    c->allocs.clear();
+}
+
+}  // namespace
+
+extern "C" {
+
+int igapw_create(igapw_ctx** out, const igapw_desc* desc, void* cuda_stream) {
+    if (!out) return fail(nullptr, IGAPW_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    std::string why;
+    if (!valid_desc(desc, why)) return fail(nullptr, IGAPW_ERR_ARG, why);
+    igapw_ctx* c = new (std::nothrow) igapw_ctx();
+    if (!c) return fail(nullptr, IGAPW_ERR_OOM, "host allocation failed");
+    c->d = *desc;
+    c->stream = (cudaStream_t)cuda_stream;
+    c->dim = desc->dim;
+    c->p = desc->degree;
+    c->ntot = 1;
+    for (int a = 0; a < 3; ++a) {
+        c->n[a] = a < c->dim ? desc->n_elem[a] + desc->degree : 1;
+        c->ntot *= c->n[a];
+    }
+    int rc = IGAPW_OK;
+    cudaError_t e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) rc = fail(c, IGAPW_ERR_CUDA, std::string("stream: ") + cudaGetErrorString(e));
+    if (!rc) {
+        e = dalloc(c, &c->status, 1);
+        if (e == cudaSuccess) e = cudaMemsetAsync(c->status, 0, sizeof(unsigned), c->stream);
+        if (e != cudaSuccess) rc = fail(c, IGAPW_ERR_CUDA, std::string("status: ") + cudaGetErrorString(e));
+    }
+    if (!rc) rc = setup_all(c, nullptr, -1);
+    if (!rc) rc = alloc_scratch(c);
+    if (rc) {
+        g_create_error = c->err;
+        release(c);
+        if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+        delete c;
+        return rc;
+    }
+    *out = c;
+    return IGAPW_OK;
+}
+
+int igapw_set_knots(igapw_ctx* c, int axis, const double* knots, int len) {
+    if (!c) return fail(nullptr, IGAPW_ERR_ARG, "ctx is NULL");
+    if (axis < 0 || axis >= c->dim || !knots || len <= 0) return fail(c, IGAPW_ERR_ARG, "bad axis or knots");
+    CKC(c, cudaStreamSynchronize(c->stream));
+    std::vector<double> kn(knots, knots + len);
+    AxisSetup trial;
+    std::string e = build_axis(trial, c->d.n_elem[axis], c->d.degree, c->d.nq, c->d.test, c->d.bc, kn);
+    if (!e.empty()) return fail(c, IGAPW_ERR_ARG, e);
+    // rebuild every axis (the padded window width is shared); keep other axes' knots
+    std::vector<std::vector<double>> keep(3);
+    for (int a = 0; a < c->dim; ++a) keep[a] = c->ax[a].knots;
+    keep[axis] = kn;
+    free_graphs(c);
+    release(c);
+    CKC(c, dalloc(c, &c->status, 1));
+    CKC(c, cudaMemsetAsync(c->status, 0, sizeof(unsigned), c->stream));
+    int wmax = 0, wqmax = 0;
+    for (int a = 0; a < c->dim; ++a) {
+        std::string err = build_axis(c->ax[a], c->d.n_elem[a], c->d.degree, c->d.nq, c->d.test, c->d.bc, keep[a]);
+        if (!err.empty()) return fail(c, IGAPW_ERR_ARG, err);
+        wmax = std::max(wmax, c->ax[a].w);
+        wqmax = std::max(wqmax, c->ax[a].wq);
+    }
+    c->W = pad_width(wmax);
+    c->WQ = std::max(wqmax, 1);
+    if (c->W < 0) return fail(c, IGAPW_ERR_ARG, "window too wide");
+    for (int a = 0; a < c->dim; ++a)
+        if (!set_window(c->ax[a], c->W)) return fail(c, IGAPW_ERR_ARG, "banded window layout failed");
+    for (int a = 0; a < c->dim; ++a) {
+        int rc = build_axis_device(c, a);
+        if (rc) return rc;
+    }
+    c->r = c->w = c->state = c->src0 = c->src1 = nullptr;
+    c->u0 = c->rho = nullptr;
+    c->src_bytes = 0;
+    int rc = check_setup_status(c);
+    if (rc) return rc;
+    return alloc_scratch(c);
+}
+
+int igapw_quad_points(igapw_ctx* c, int axis, double* x, double* w, int* count) {
+    if (!c) return fail(nullptr, IGAPW_ERR_ARG, "ctx is NULL");
+    if (axis < 0 || axis >= c->dim || !count) return fail(c, IGAPW_ERR_ARG, "bad axis or count");
+    const AxisSetup& s = c->ax[axis];
+    *count = (int)s.qx.size();
+    if (x) std::memcpy(x, s.qx.data(), s.qx.size() * sizeof(double));
+    if (w) std::memcpy(w, s.qw.data(), s.qw.size() * sizeof(double));
+    return IGAPW_OK;
+}
+
+int igapw_basis_table(igapw_ctx* c, int axis, double* vals, int* first_fn) {
+    if (!c) return fail(nullptr, IGAPW_ERR_ARG, "ctx is NULL");
+    if (axis < 0 || axis >= c->dim) return fail(c, IGAPW_ERR_ARG, "bad axis");
+    const AxisSetup& s = c->ax[axis];
+    if (vals) {
+        CKC(c, cudaStreamSynchronize(c->stream));
+        CKC(c, cudaMemcpy(vals, c->mem[axis].vals, s.qx.size() * (s.p + 1) * 3 * sizeof(double),
+                          cudaMemcpyDeviceToHost));
+    }
+    if (first_fn) std::memcpy(first_fn, s.qfirst.data(), s.qfirst.size() * sizeof(int));
+    return IGAPW_OK;
+}
+
+int igapw_rhs_source(igapw_ctx* c, const void* f_dev, void* b_dev) {
+    if (!c) return fail(nullptr, IGAPW_ERR_ARG, "ctx is NULL");
+    if (!f_dev || !b_dev) return fail(c, IGAPW_ERR_ARG, "NULL tensor");
+    SourceArgs a{};
+    a.dim = c->dim;
+    long long q[3] = {1, 1, 1};
+    for (int k = 0; k < 3; ++k) {
+        a.n[k] = c->n[k];
+        a.q[k] = k < c->dim ? (int)c->ax[k].qx.size() : 1;
+        q[k] = a.q[k];
+        a.ax[k] = c->dev[k];
+    }
+    // intermediates: after the x pass (q_z q_y n_x), after the y pass (q_z n_y n_x)
+    const size_t need = 8 * (size_t)std::max(q[2] * q[1] * c->n[0], q[2] * c->n[1] * c->n[0]);
+    if (c->dim > 1 && c->src_bytes < need) {
+        CKC(c, cudaStreamSynchronize(c->stream));
+        unsigned char *b0 = nullptr, *b1 = nullptr;
+        CKC(c, dalloc(c, &b0, need));
+        CKC(c, dalloc(c, &b1, need));
+        c->src0 = b0;
+        c->src1 = b1;
+        c->src_bytes = need;
+    }
+    a.f = f_dev;
+    a.out = b_dev;
+    a.work0 = c->src0;
+    a.work1 = c->src1;
+    a.ntot = c->ntot;
+    cudaError_t e = launch_source(a, fp64(c), c->stream);
+    if (e != cudaSuccess) return fail(c, IGAPW_ERR_CUDA, std::string("source: ") + cudaGetErrorString(e));
+    return IGAPW_OK;
+}
+
+int igapw_apply(igapw_ctx* c, int op, double dt, const void* u_dev, void* r_dev) {
+    if (!c) return fail(nullptr, IGAPW_ERR_ARG, "ctx is NULL");
+    if (!u_dev || !r_dev) return fail(c, IGAPW_ERR_ARG, "NULL tensor");
+    if (u_dev == r_dev) return fail(c, IGAPW_ERR_ARG, "u and r must not overlap");
+    switch (op) {
+        case IGAPW_OP_MASS: return enqueue_apply(c, MODE_OP, 1.0, 0.0, u_dev, r_dev, c->stream);
+        case IGAPW_OP_LAPLACE: return enqueue_apply(c, MODE_OP, 0.0, 1.0, u_dev, r_dev, c->stream);
+        case IGAPW_OP_HEAT: return enqueue_apply(c, MODE_OP, 1.0, dt, u_dev, r_dev, c->stream);
+        case IGAPW_OP_POISSON:
+            if (c->d.op != IGAPW_OP_POISSON) return fail(c, IGAPW_ERR_ARG, "POISSON apply needs a POISSON context");
+            return enqueue_apply(c, MODE_SYS, 1.0, 0.0, u_dev, r_dev, c->stream);
+    }
+    return fail(c, IGAPW_ERR_ARG, "unknown op");
+}
+
+int igapw_assemble_1d(igapw_ctx* c, int axis, int which, double* dense) {
+    if (!c) return fail(nullptr, IGAPW_ERR_ARG, "ctx is NULL");
+    if (axis < 0 || axis >= c->dim || !dense) return fail(c, IGAPW_ERR_ARG, "bad axis or output");
+    const double* src = nullptr;
+    if (which == IGAPW_OP_MASS) src = c->mem[axis].A;
+    else if (which == IGAPW_OP_LAPLACE) src = c->mem[axis].C;
+    else if (which == IGAPW_OP_POISSON && c->d.op == IGAPW_OP_POISSON) src = c->mem[axis].S;
+    else return fail(c, IGAPW_ERR_ARG, "which must be MASS, LAPLACE or (POISSON context) POISSON");
+    const int n = c->ax[axis].n, W = c->W;
+    std::vector<double> win((size_t)n * W);
+    CKC(c, cudaStreamSynchronize(c->stream));
+    CKC(c, cudaMemcpy(win.data(), src, win.size() * sizeof(double), cudaMemcpyDeviceToHost));
+    std::memset(dense, 0, (size_t)n * n * sizeof(double));
+    for (int i = 0; i < n; ++i)
+        for (int w = 0; w < W; ++w) {
+            const int j = c->ax[axis].fstart[i] + w;
+            if (j < n) dense[(size_t)i * n + j] = win[(size_t)i * W + w];
+        }
+    return IGAPW_OK;
+}
+
+int igapw_solve(igapw_ctx* c, const void* r_dev, void* u_dev) {
+    if (!c) return fail(nullptr, IGAPW_ERR_ARG, "ctx is NULL");
+    if (!r_dev || !u_dev) return fail(c, IGAPW_ERR_ARG, "NULL tensor");
+    return enqueue_solve(c, r_dev, u_dev, c->stream);
+}
+
+int igapw_step(igapw_ctx* c, double dt, int nsteps, void* u_dev) {
+    if (!c) return fail(nullptr, IGAPW_ERR_ARG, "ctx is NULL");
+    if (!u_dev || nsteps < 0) return fail(c, IGAPW_ERR_ARG, "bad arguments");
+    if (nsteps == 0) return IGAPW_OK;
+    // graphs of up to CHUNK steps, replayed
+    const int CHUNK = 50;
+    int left = nsteps;
+    while (left > 0) {
+        const int k = left < CHUNK ? left : CHUNK;
+        cudaGraphExec_t exec = nullptr;
+        for (auto& g : c->graphs)
+            if (g.dt == dt && g.nsteps == k && g.u == u_dev) exec = g.exec;
+        if (!exec) {
+            CKC(c, cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeRelaxed));
+            int rc = enqueue_steps(c, dt, k, u_dev, c->cap_stream);
+            cudaGraph_t graph = nullptr;
+            cudaError_t e = cudaStreamEndCapture(c->cap_stream, &graph);
+            if (rc) { if (graph) cudaGraphDestroy(graph); return rc; }
+            CKC(c, e);
+            e = cudaGraphInstantiate(&exec, graph, 0);
+            cudaGraphDestroy(graph);
+            CKC(c, e);
+            if (c->graphs.size() >= 16) free_graphs(c);
+            c->graphs.push_back({dt, k, u_dev, exec});
+        }
+        CKC(c, cudaGraphLaunch(exec, c->stream));
+        left -= k;
+    }
+    return IGAPW_OK;
+}
+
+int igapw_step_host(igapw_ctx* c, double dt, int nsteps, void* u_host) {
+    if (!c) return fail(nullptr, IGAPW_ERR_ARG, "ctx is NULL");
+    if (!u_host) return fail(c, IGAPW_ERR_ARG, "NULL host buffer");
+    const size_t bytes = fp64(c) ? (size_t)c->ntot * 8 : (size_t)c->ntot * 8;
+    if (!c->state) {
+        unsigned char* s = nullptr;
+        CKC(c, dalloc(c, &s, bytes));
+        c->state = s;
+    }
+    CKC(c, cudaMemcpyAsync(c->state, u_host, bytes, cudaMemcpyHostToDevice, c->stream));
+    int rc = igapw_step(c, dt, nsteps, c->state);
+    if (rc) return rc;
+    CKC(c, cudaMemcpyAsync(u_host, c->state, bytes, cudaMemcpyDeviceToHost, c->stream));
+    CKC(c, cudaStreamSynchronize(c->stream));
+    return IGAPW_OK;
+}
+
+int igapw_sync_status(igapw_ctx* c) {
+    if (!c) return fail(nullptr, IGAPW_ERR_ARG, "ctx is NULL");
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return fail(c, IGAPW_ERR_CUDA, std::string("async error: ") + cudaGetErrorString(e));
+    unsigned st = 0;
+    CKC(c, cudaMemcpy(&st, c->status, sizeof st, cudaMemcpyDeviceToHost));
+    if (st) {
+        unsigned z = 0;
+        CKC(c, cudaMemcpy(c->status, &z, sizeof z, cudaMemcpyHostToDevice));
+        if (st & STATUS_NONFINITE) return fail(c, IGAPW_ERR_DEVICE_STATUS, "a solve produced a non-finite value");
+        return fail(c, IGAPW_ERR_DEVICE_STATUS, "device status " + std::to_string(st));
+    }
+    return IGAPW_OK;
+}
+
+const char* igapw_last_error(igapw_ctx* c) {
+    if (!c) return g_create_error.c_str();
+    return c->err.c_str();
+}
+
+long long igapw_size(igapw_ctx* c, int* dims) {
+    if (!c) return -1;
+    if (dims)
+        for (int a = 0; a < 3; ++a) dims[a] = c->n[a];
+    return c->ntot;
+}
+
+int igapw_destroy(igapw_ctx* c) {
+    if (!c) return IGAPW_OK;
+    cudaStreamSynchronize(c->stream);
+    release(c);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+    delete c;
+    return IGAPW_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,128 @@
+// Shared device definitions: double-float (FP32 pair) arithmetic, per-axis
+// device descriptors, and the status word.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace igapw {
+
+// ---------------------------------------------------------------------------
+// Double-float arithmetic.  A value is hi + lo with |lo| <= ulp(hi)/2.
+// Error-free transforms: the product of two floats is p + e exactly with
+// p = a*b, e = fma(a, b, -p) (the FMA is exact up to its final rounding);
+// the sum of two floats is s + e exactly with Knuth's branch-free two-sum.
+// Built without fast-math, so these expressions are evaluated as written.
+// ---------------------------------------------------------------------------
+struct DF {
+    float hi, lo;
+};
+
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = a + b;
+    float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+
+__device__ __forceinline__ void fast_two_sum(float a, float b, float& s, float& e) {
+    s = a + b;
+    e = b - (s - a);
+}
+
+__device__ __forceinline__ DF df_make(float hi, float lo) {
+    DF r;
+    fast_two_sum(hi, lo, r.hi, r.lo);
+    return r;
+}
+
+// Accumulator of a compensated dot product: running sum s with the exact
+// rounding errors of every addition and product collected in c.
+struct DFAcc {
+    float s, c;
+    __device__ __forceinline__ void init() { s = 0.f; c = 0.f; }
+    // s + c += t * v with t, v double-float: the hi*hi product is split exactly,
+    // the cross terms hi*lo + lo*hi enter c directly (lo*lo is below 2^-48).
+    __device__ __forceinline__ void add_prod(DF t, DF v) {
+        float p = t.hi * v.hi;
+        float e = fmaf(t.hi, v.hi, -p);
+        e = fmaf(t.hi, v.lo, e);
+        e = fmaf(t.lo, v.hi, e);
+        float s2, err;
+        two_sum(s, p, s2, err);
+        s = s2;
+        c += err + e;
+    }
+    // s + c += v
+    __device__ __forceinline__ void add(DF v) {
+        float s2, err;
+        two_sum(s, v.hi, s2, err);
+        s = s2;
+        c += err + v.lo;
+    }
+    __device__ __forceinline__ DF result() const { return df_make(s, c); }
+};
+
+__device__ __forceinline__ DF df_add(DF a, DF b) {
+    float s, e;
+    two_sum(a.hi, b.hi, s, e);
+    e += a.lo + b.lo;
+    return df_make(s, e);
+}
+
+__device__ __forceinline__ DF df_mul(DF a, DF b) {
+    float p = a.hi * b.hi;
+    float e = fmaf(a.hi, b.hi, -p);
+    e = fmaf(a.hi, b.lo, e);
+    e = fmaf(a.lo, b.hi, e);
+    return df_make(p, e);
+}
+
+__host__ __device__ inline void split_double(double v, float& hi, float& lo) {
+    hi = (float)v;
+    lo = (float)(v - (double)hi);
+}
+
+// ---------------------------------------------------------------------------
+// Per-axis device tables.  Window format: row i couples to columns
+// [fstart[i], fstart[i] + W) with W the padded kernel width of the context.
+// ---------------------------------------------------------------------------
+struct TableSet {
+    const double* d;   // FP64 [n * W]
+    const float* hi;   // FP32 pair hi [n * W]
+    const float* lo;   // FP32 pair lo [n * W]
+};
+
+// Precomputed data of the partitioned banded solve of one 1D system
+// (banded LU without pivoting, KL = KU = p).  Rows are split into P <= 32
+// chunks b[k] .. b[k+1]-1, one per lane of a warp.
+template <typename T>
+struct LineSys {
+    int n, P;
+    int b[33];
+    const T* L;      // [n * p]   L[i*p + m-1] = l_{i, i-m}
+    const T* U;      // [n * p]   U[i*p + m-1] = u_{i, i+m}
+    const T* dinv;   // [n]       1 / u_{i,i}
+    const T* G;      // [n * p]   forward spike: y_i -= sum_c G[i*p+c] * tail_{k-1}[c]
+    const T* H;      // [n * p]   backward spike: x_i -= sum_c H[i*p+c] * head_{k+1}[c]
+    const T* PhiF;   // [5 * 32 * p * p] forward scan operators per level and lane
+    const T* PhiB;   // [5 * 32 * p * p] backward scan operators
+};
+
+struct AxisDev {
+    int n;          // coefficients on this axis
+    int nq;         // quadrature points on this axis
+    int wq;         // point-window width (padded)
+    const int* fstart;   // [n]
+    const int* pstart;   // [n]
+    const int* is_free;  // [n]
+    TableSet A;     // int T_i B_j        (Dirichlet rows: identity)
+    TableSet C;     // int T_i B_j''      (Dirichlet rows: zero)
+    TableSet S;     // system matrix factored for the solve
+    TableSet TW;    // test weights over the point window [n * wq]
+    LineSys<double> ls64;
+    LineSys<float> ls32;
+};
+
+// Status bits written by kernels (read back by igapw_sync_status).
+enum : unsigned { STATUS_NONFINITE = 1u, STATUS_SINGULAR = 2u };
+
+}  // namespace igapw

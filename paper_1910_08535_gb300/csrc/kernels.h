@@ -1,0 +1,96 @@
+// Internal launch interface between the C ABI (api.cu) and the kernels.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+#define IGAPW_MAXP 4
+
+namespace igapw {
+
+struct FoldArgs {
+    int n, p, W, WQ, test, poisson;
+    const int* fstart;
+    const int* pstart;
+    const int* pcount;
+    const int* is_free;
+    const int* qfirst;
+    const double* qw;
+    const double* vals;
+    double *A, *C, *S, *TW;
+    float *Ahi, *Alo, *Chi, *Clo, *Shi, *Slo, *TWhi, *TWlo;
+};
+
+struct FactorArgs {
+    int n, p, W, P;
+    int b[33];
+    const int* fstart;
+    const double* S;
+    double* work;
+    double *L, *U, *dinv, *G, *H, *PhiF, *PhiB;
+    float *L32, *U32, *dinv32, *G32, *H32, *PhiF32, *PhiB32;
+    unsigned* status;
+};
+
+void launch_basis_table(const double* t, int p, int Q, const double* qx, const int* qfirst,
+                        double* vals, cudaStream_t st);
+void launch_fold(const FoldArgs& f, cudaStream_t st);
+void launch_factor(const FactorArgs& a, cudaStream_t st);
+
+// ---- sum-factorised contractions (rhs.cu) ----------------------------------
+// MODE_OP:  r = T(alpha u + beta Lap u) with the folded A / C tables
+// MODE_SYS: r = (S_z (x) S_y (x) S_x) u with the system tables
+// MODE_RES: rho = r - (S_z (x) S_y (x) S_x) u0   (refinement residual)
+enum { MODE_OP = 0, MODE_SYS = 1, MODE_RES = 2 };
+// compute / storage formats
+enum { FMT_F64 = 0, FMT_PAIR = 1, FMT_F32 = 2 };
+
+struct ContractArgs {
+    int dim, W;
+    int n[3];               // n_x, n_y, n_z
+    int zchunk;
+    AxisDev ax[3];
+    const void* u;          // MODE_OP/SYS: F64 or PAIR; MODE_RES: F32 u0
+    const void* r;          // MODE_RES: PAIR right-hand side
+    void* out;              // F64 / PAIR / F32 (MODE_RES)
+    long long ntot;         // elements per plane of a pair tensor
+    double alpha, beta;
+};
+
+// cmp: FMT_F64 (double arithmetic) or FMT_PAIR (double-float arithmetic);
+// io: FMT_F64 (double tensors) or FMT_PAIR (pair tensors; MODE_RES reads
+// F32 u0 + PAIR r and writes F32).  Returns a CUDA error code.
+cudaError_t launch_contract(const ContractArgs& a, int mode, int cmp, int io, cudaStream_t st);
+
+// ---- source right-hand side (rhs.cu) ----------------------------------------
+// b = (TW_z (x) TW_y (x) TW_x) f over the quadrature grid, one axis per pass.
+struct SourceArgs {
+    int dim;
+    int n[3];               // coefficients per axis
+    int q[3];               // points per axis
+    AxisDev ax[3];
+    const void* f;          // F64 or F32 samples, x fastest
+    void* out;              // F64 or PAIR
+    void* work0;            // scratch, >= max intermediate size (doubles or pairs)
+    void* work1;
+    long long ntot;
+};
+cudaError_t launch_source(const SourceArgs& a, int fp64, cudaStream_t st);
+
+// ---- line solves (solve.cu) -------------------------------------------------
+// Solves along one axis of a (n_z, n_y, n_x) tensor with the axis' LU.
+//   in_fmt  FMT_F64 | FMT_F32 | FMT_PAIR (hi plane read as FP32)
+//   out_fmt FMT_F64 | FMT_F32 | FMT_PAIR (finish: out = u0 + x as a pair, u0 F32)
+struct SolveArgs {
+    int axis;
+    int n[3];
+    const void* in;
+    void* out;
+    const float* u0;        // finish epilogue only
+    long long ntot;
+    unsigned* status;
+};
+cudaError_t launch_solve(const SolveArgs& s, const AxisDev& ax, int p, int in_fmt, int out_fmt,
+                         bool fp64, cudaStream_t st);
+
+}  // namespace igapw

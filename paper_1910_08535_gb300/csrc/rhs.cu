@@ -1,0 +1,446 @@
+// Kernel (b): sum-factorised per-axis contractions of the coefficient tensor
+// with the folded quadrature tables.
+//
+// Operator action (MODE_OP).  The tested operator of u + beta Lap u with tests
+// T = T_x T_y T_z (PW indicators or B-splines) factorises per axis into the
+// folded tables A = int T_i B_j and C = int T_i B_j'':
+//   r = A_x [ alpha A_y A_z u + beta (C_y A_z u + A_y C_z u) ] + beta C_x [ A_y A_z u ]
+// computed as z-pass (ZA = A_z u, ZC = C_z u), y-pass (Q1 = A_y ZA,
+// Q2 = alpha Q1 + beta (C_y ZA + A_y ZC)), x-pass (r = A_x Q2 + beta C_x Q1):
+// 7 banded passes.  The quadrature itself lives in the tables: kernel (a)
+// summed w_q B_j(x_q) over each cell (PW: the test is 1) or multiplied by the
+// test B-spline (Galerkin).
+//
+// A block owns an x-tile x a y-tile of outputs for a chunk of z-planes.  It
+// streams z: a ring of W input planes (with the x/y halo the windows need) is
+// refilled one plane at a time, so every input plane is read once per block.
+//
+// MODE_SYS applies the factored system S_z S_y S_x; MODE_RES forms the
+// refinement residual r - S u0 (FP64 or double-float arithmetic).
+#include <type_traits>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace igapw {
+
+template <typename CT>
+struct Acc;
+template <>
+struct Acc<double> {
+    double s;
+    __device__ __forceinline__ void init() { s = 0.0; }
+    __device__ __forceinline__ void add_prod(double t, double v) { s = fma(t, v, s); }
+    __device__ __forceinline__ void add(double v) { s += v; }
+    __device__ __forceinline__ double result() const { return s; }
+};
+template <>
+struct Acc<DF> : DFAcc {};
+
+template <typename CT>
+struct SBuf;
+template <>
+struct SBuf<double> {
+    double* p;
+    __device__ __forceinline__ double ld(int i) const { return p[i]; }
+    __device__ __forceinline__ void st(int i, double v) const { p[i] = v; }
+    static constexpr int bytes = 8;
+    __device__ __forceinline__ void carve(unsigned char*& base, int count) {
+        p = reinterpret_cast<double*>(base);
+        base += (size_t)count * 8;
+    }
+};
+template <>
+struct SBuf<DF> {
+    float* h;
+    float* l;
+    __device__ __forceinline__ DF ld(int i) const { return DF{h[i], l[i]}; }
+    __device__ __forceinline__ void st(int i, DF v) const { h[i] = v.hi; l[i] = v.lo; }
+    static constexpr int bytes = 8;
+    __device__ __forceinline__ void carve(unsigned char*& base, int count) {
+        h = reinterpret_cast<float*>(base);
+        l = h + count;
+        base += (size_t)count * 8;
+    }
+};
+
+template <typename CT>
+__device__ __forceinline__ CT tab(const TableSet& t, int idx);
+template <>
+__device__ __forceinline__ double tab<double>(const TableSet& t, int idx) { return __ldg(t.d + idx); }
+template <>
+__device__ __forceinline__ DF tab<DF>(const TableSet& t, int idx) { return DF{__ldg(t.hi + idx), __ldg(t.lo + idx)}; }
+
+template <typename CT>
+__device__ __forceinline__ CT zero_v();
+template <>
+__device__ __forceinline__ double zero_v<double>() { return 0.0; }
+template <>
+__device__ __forceinline__ DF zero_v<DF>() { return DF{0.f, 0.f}; }
+
+template <typename CT>
+__device__ __forceinline__ CT from_double(double v);
+template <>
+__device__ __forceinline__ double from_double<double>(double v) { return v; }
+template <>
+__device__ __forceinline__ DF from_double<DF>(double v) {
+    DF r;
+    split_double(v, r.hi, r.lo);
+    return r;
+}
+
+// coefficient input u (MODE_OP / MODE_SYS) or u0 (MODE_RES)
+template <typename CT, int MODE, int IO>
+__device__ __forceinline__ CT load_u(const ContractArgs& a, long long g) {
+    if constexpr (MODE == MODE_RES) {
+        const float v = ((const float*)a.u)[g];
+        if constexpr (std::is_same<CT, double>::value) return (double)v;
+        else return DF{v, 0.f};
+    } else if constexpr (IO == FMT_F64) {
+        return ((const double*)a.u)[g];
+    } else {
+        const float* u = (const float*)a.u;
+        return DF{u[g], u[g + a.ntot]};
+    }
+}
+
+template <typename CT, int MODE, int IO>
+__device__ __forceinline__ void store_r(const ContractArgs& a, long long g, CT v) {
+    if constexpr (MODE == MODE_RES) {
+        const float* r = (const float*)a.r;
+        if constexpr (std::is_same<CT, DF>::value) {
+            DFAcc acc;
+            acc.s = r[g];
+            acc.c = r[g + a.ntot];
+            acc.add(DF{-v.hi, -v.lo});
+            ((float*)a.out)[g] = acc.result().hi;
+        } else {
+            const double rr = (double)r[g] + (double)r[g + a.ntot];
+            ((float*)a.out)[g] = (float)(rr - v);
+        }
+    } else if constexpr (IO == FMT_F64) {
+        ((double*)a.out)[g] = v;
+    } else {
+        ((float*)a.out)[g] = v.hi;
+        ((float*)a.out)[g + a.ntot] = v.lo;
+    }
+}
+
+template <int DIM, int W, int TX, int TY, typename CT, int MODE, int IO>
+__global__ void __launch_bounds__(256) contract_kernel(const ContractArgs a) {
+    constexpr bool OP = (MODE == MODE_OP);
+    constexpr int XH = TX + W - 1;
+    constexpr int YH = DIM >= 2 ? TY + W - 1 : 1;
+    constexpr int TYE = DIM >= 2 ? TY : 1;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+
+    const int nx = a.n[0], ny = a.n[1], nz = a.n[2];
+    const AxisDev& AX = a.ax[0];
+    const AxisDev& AY = a.ax[1];
+    const AxisDev& AZ = a.ax[2];
+    const int x0 = blockIdx.x * TX;
+    const int y0 = DIM >= 2 ? blockIdx.y * TY : 0;
+    const int nxo = min(TX, nx - x0);
+    const int nyo = DIM >= 2 ? min(TY, ny - y0) : 1;
+    const int xl = AX.fstart[x0];
+    const int nxh = AX.fstart[x0 + nxo - 1] + W - xl;
+    const int yl = DIM >= 2 ? AY.fstart[y0] : 0;
+    const int nyh = DIM >= 2 ? AY.fstart[y0 + nyo - 1] + W - yl : 1;
+    const long long plane = (long long)nx * ny;
+
+    unsigned char* base = smem_raw;
+    SBuf<CT> ring, ZA, ZC, Q1, Q2;
+    if constexpr (DIM == 3) ring.carve(base, W * YH * XH);
+    if constexpr (DIM >= 2) ZA.carve(base, YH * XH);
+    if constexpr (DIM == 3 && OP) ZC.carve(base, YH * XH);
+    Q1.carve(base, TYE * XH);
+    if constexpr (OP) Q2.carve(base, TYE * XH);
+
+    const CT alpha = from_double<CT>(a.alpha);
+    const CT beta = from_double<CT>(a.beta);
+    const TableSet& TXa = OP ? AX.A : AX.S;
+    const TableSet& TYa = OP ? AY.A : AY.S;
+    const TableSet& TZa = OP ? AZ.A : AZ.S;
+
+    // x-pass over the y-rows of Q1/Q2 for output plane zo, then store
+    auto x_pass = [&](int zo) {
+        for (int e = threadIdx.x; e < nyo * nxo; e += blockDim.x) {
+            const int y = e / nxo, x = e - y * nxo;
+            const int xc = x0 + x;
+            const int sx = AX.fstart[xc] - xl;
+            const int qb = y * XH + sx;
+            Acc<CT> r1, r2;
+            r1.init();
+            r2.init();
+#pragma unroll
+            for (int w = 0; w < W; ++w) {
+                if constexpr (OP) {
+                    r1.add_prod(tab<CT>(AX.A, xc * W + w), Q2.ld(qb + w));
+                    r2.add_prod(tab<CT>(AX.C, xc * W + w), Q1.ld(qb + w));
+                } else {
+                    r1.add_prod(tab<CT>(AX.S, xc * W + w), Q1.ld(qb + w));
+                }
+            }
+            CT v;
+            if constexpr (OP) {
+                Acc<CT> t;
+                t.init();
+                t.add(r1.result());
+                t.add_prod(beta, r2.result());
+                v = t.result();
+            } else {
+                v = r1.result();
+            }
+            const long long g = (long long)zo * plane + (long long)(y0 + y) * nx + xc;
+            store_r<CT, MODE, IO>(a, g, v);
+        }
+    };
+
+    // y-pass: ZA (and ZC) rows -> Q1 (and Q2)
+    auto y_pass = [&]() {
+        for (int e = threadIdx.x; e < nyo * nxh; e += blockDim.x) {
+            const int y = e / nxh, xx = e - y * nxh;
+            const int yr = y0 + y;
+            const int sy = AY.fstart[yr] - yl;
+            Acc<CT> q1;
+            q1.init();
+            if constexpr (OP) {
+                Acc<CT> t2;
+                t2.init();
+#pragma unroll
+                for (int w = 0; w < W; ++w) {
+                    const CT za = ZA.ld((sy + w) * XH + xx);
+                    q1.add_prod(tab<CT>(AY.A, yr * W + w), za);
+                    t2.add_prod(tab<CT>(AY.C, yr * W + w), za);
+                    if constexpr (DIM == 3) t2.add_prod(tab<CT>(AY.A, yr * W + w), ZC.ld((sy + w) * XH + xx));
+                }
+                const CT v1 = q1.result();
+                Acc<CT> q2;
+                q2.init();
+                q2.add_prod(alpha, v1);
+                q2.add_prod(beta, t2.result());
+                Q1.st(y * XH + xx, v1);
+                Q2.st(y * XH + xx, q2.result());
+            } else {
+#pragma unroll
+                for (int w = 0; w < W; ++w) q1.add_prod(tab<CT>(TYa, yr * W + w), ZA.ld((sy + w) * XH + xx));
+                Q1.st(y * XH + xx, q1.result());
+            }
+        }
+    };
+
+    if constexpr (DIM == 1) {
+        for (int e = threadIdx.x; e < nxh; e += blockDim.x) {
+            const int gx = xl + e;
+            const CT v = gx < nx ? load_u<CT, MODE, IO>(a, gx) : zero_v<CT>();
+            Q1.st(e, v);
+            if constexpr (OP) {
+                Acc<CT> t;
+                t.init();
+                t.add_prod(alpha, v);
+                Q2.st(e, t.result());
+            }
+        }
+        __syncthreads();
+        x_pass(0);
+    } else if constexpr (DIM == 2) {
+        for (int e = threadIdx.x; e < nyh * nxh; e += blockDim.x) {
+            const int yy = e / nxh, xx = e - yy * nxh;
+            const int gy = yl + yy, gx = xl + xx;
+            ZA.st(yy * XH + xx, (gy < ny && gx < nx) ? load_u<CT, MODE, IO>(a, (long long)gy * nx + gx) : zero_v<CT>());
+        }
+        __syncthreads();
+        y_pass();
+        __syncthreads();
+        x_pass(0);
+    } else {
+        const int z0 = blockIdx.z * a.zchunk;
+        const int z1 = min(z0 + a.zchunk, nz);
+        int rhi = AZ.fstart[z0];
+        for (int zo = z0; zo < z1; ++zo) {
+            const int zs = AZ.fstart[zo];
+            while (rhi < zs + W) {
+                const int slot = (rhi % W) * (YH * XH);
+                for (int e = threadIdx.x; e < nyh * nxh; e += blockDim.x) {
+                    const int yy = e / nxh, xx = e - yy * nxh;
+                    const int gy = yl + yy, gx = xl + xx;
+                    CT v = zero_v<CT>();
+                    if (rhi < nz && gy < ny && gx < nx)
+                        v = load_u<CT, MODE, IO>(a, (long long)rhi * plane + (long long)gy * nx + gx);
+                    ring.st(slot + yy * XH + xx, v);
+                }
+                ++rhi;
+            }
+            __syncthreads();
+            // z-pass
+            for (int e = threadIdx.x; e < nyh * nxh; e += blockDim.x) {
+                const int yy = e / nxh, xx = e - yy * nxh;
+                const int off = yy * XH + xx;
+                Acc<CT> za, zc;
+                za.init();
+                zc.init();
+#pragma unroll
+                for (int w = 0; w < W; ++w) {
+                    const CT v = ring.ld(((zs + w) % W) * (YH * XH) + off);
+                    za.add_prod(tab<CT>(TZa, zo * W + w), v);
+                    if constexpr (OP) zc.add_prod(tab<CT>(AZ.C, zo * W + w), v);
+                }
+                ZA.st(off, za.result());
+                if constexpr (OP) ZC.st(off, zc.result());
+            }
+            __syncthreads();
+            y_pass();
+            __syncthreads();
+            x_pass(zo);
+            __syncthreads();
+        }
+    }
+}
+
+template <int DIM, int W, int TX, int TY, typename CT, int MODE, int IO>
+static cudaError_t run_contract(const ContractArgs& a, cudaStream_t st) {
+    constexpr bool OP = (MODE == MODE_OP);
+    constexpr int XH = TX + W - 1;
+    constexpr int YH = DIM >= 2 ? TY + W - 1 : 1;
+    constexpr int TYE = DIM >= 2 ? TY : 1;
+    size_t elems = 0;
+    if (DIM == 3) elems += (size_t)W * YH * XH;
+    if (DIM >= 2) elems += (size_t)YH * XH;
+    if (DIM == 3 && OP) elems += (size_t)YH * XH;
+    elems += (size_t)TYE * XH * (OP ? 2 : 1);
+    const size_t sm = elems * 8;
+    auto k = contract_kernel<DIM, W, TX, TY, CT, MODE, IO>;
+    if (sm > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return e;
+    }
+    dim3 grid((a.n[0] + TX - 1) / TX, DIM >= 2 ? (a.n[1] + TY - 1) / TY : 1,
+              DIM == 3 ? (a.n[2] + a.zchunk - 1) / a.zchunk : 1);
+    k<<<grid, 256, sm, st>>>(a);
+    return cudaGetLastError();
+}
+
+template <int DIM, int W, typename CT, int MODE, int IO>
+static cudaError_t pick_tile(const ContractArgs& a, cudaStream_t st) {
+    if constexpr (DIM == 1) return run_contract<1, W, 256, 1, CT, MODE, IO>(a, st);
+    else if constexpr (DIM == 2) return run_contract<2, W, 64, 8, CT, MODE, IO>(a, st);
+    else return run_contract<3, W, 32, 8, CT, MODE, IO>(a, st);
+}
+
+template <int DIM, int W>
+static cudaError_t dispatch_mode(const ContractArgs& a, int mode, int cmp, int io, cudaStream_t st) {
+    if (mode == MODE_RES) {
+        if (cmp == FMT_F64) return pick_tile<DIM, W, double, MODE_RES, FMT_PAIR>(a, st);
+        return pick_tile<DIM, W, DF, MODE_RES, FMT_PAIR>(a, st);
+    }
+    if (io == FMT_F64) {
+        if (mode == MODE_OP) return pick_tile<DIM, W, double, MODE_OP, FMT_F64>(a, st);
+        return pick_tile<DIM, W, double, MODE_SYS, FMT_F64>(a, st);
+    }
+    if (mode == MODE_OP) return pick_tile<DIM, W, DF, MODE_OP, FMT_PAIR>(a, st);
+    return pick_tile<DIM, W, DF, MODE_SYS, FMT_PAIR>(a, st);
+}
+
+template <int DIM>
+static cudaError_t dispatch_w(const ContractArgs& a, int mode, int cmp, int io, cudaStream_t st) {
+    switch (a.W) {
+        case 3: return dispatch_mode<DIM, 3>(a, mode, cmp, io, st);
+        case 5: return dispatch_mode<DIM, 5>(a, mode, cmp, io, st);
+        case 7: return dispatch_mode<DIM, 7>(a, mode, cmp, io, st);
+        case 9: return dispatch_mode<DIM, 9>(a, mode, cmp, io, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_contract(const ContractArgs& a, int mode, int cmp, int io, cudaStream_t st) {
+    switch (a.dim) {
+        case 1: return dispatch_w<1>(a, mode, cmp, io, st);
+        case 2: return dispatch_w<2>(a, mode, cmp, io, st);
+        case 3: return dispatch_w<3>(a, mode, cmp, io, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+// ---------------------------------------------------------------------------
+// Kernel (b-src): source right-hand side b = (TW_z TW_y TW_x) f, one pass per
+// axis.  A pass maps in[(o*Qa + q)*Ni + x] to out[(o*na + i)*Ni + x] with
+// out = sum_w TW[i][w] in[.. pstart[i] + w ..]: PW sums the weights of the
+// cell's points (test 1), Galerkin multiplies by the test B-spline.
+// ---------------------------------------------------------------------------
+template <typename CT, int IN_F32, int OUT_PLANES>
+__global__ void __launch_bounds__(256) source_pass_kernel(const void* in, void* out, long long nout_total,
+                                                          int Qa, int na, long long Ni, long long No,
+                                                          int wq, const int* __restrict__ pstart,
+                                                          TableSet tw, long long plane_out) {
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long total = No * na * Ni;
+    if (e >= total) return;
+    const long long x = e % Ni;
+    const long long t = e / Ni;
+    const int i = (int)(t % na);
+    const long long o = t / na;
+    const int ps = pstart[i];
+    Acc<CT> acc;
+    acc.init();
+    for (int w = 0; w < wq; ++w) {
+        const int q = ps + w;
+        if (q >= Qa) break;
+        const long long gi = (o * Qa + q) * Ni + x;
+        CT v;
+        if constexpr (std::is_same<CT, double>::value) {
+            v = IN_F32 ? (double)((const float*)in)[gi] : ((const double*)in)[gi];
+        } else {
+            if constexpr (IN_F32) v = DF{((const float*)in)[gi], 0.f};
+            else v = ((const DF*)in)[gi];
+        }
+        acc.add_prod(tab<CT>(tw, i * wq + w), v);
+    }
+    const CT r = acc.result();
+    if constexpr (std::is_same<CT, double>::value) {
+        ((double*)out)[e] = r;
+    } else {
+        if constexpr (OUT_PLANES) {
+            ((float*)out)[e] = r.hi;
+            ((float*)out)[e + plane_out] = r.lo;
+        } else {
+            ((DF*)out)[e] = r;
+        }
+    }
+    (void)nout_total;
+}
+
+cudaError_t launch_source(const SourceArgs& a, int fp64, cudaStream_t st) {
+    // passes: x (Ni = 1), then y (Ni = n_x), then z (Ni = n_x n_y)
+    const int d = a.dim;
+    long long dims_in[3] = {a.q[0], d >= 2 ? a.q[1] : 1, d >= 3 ? a.q[2] : 1};
+    const void* src = a.f;
+    void* bufs[2] = {a.work0, a.work1};
+    for (int ax = 0; ax < d; ++ax) {
+        long long Ni = 1, No = 1;
+        for (int k = 0; k < ax; ++k) Ni *= dims_in[k];
+        for (int k = ax + 1; k < 3; ++k) No *= dims_in[k];
+        const int Qa = (int)dims_in[ax], na = a.n[ax];
+        const bool last = (ax == d - 1);
+        void* dst = last ? a.out : bufs[ax & 1];
+        const long long total = No * na * Ni;
+        const unsigned blocks = (unsigned)((total + 255) / 256);
+        const AxisDev& A = a.ax[ax];
+        if (fp64) {
+            source_pass_kernel<double, 0, 0><<<blocks, 256, 0, st>>>(src, dst, total, Qa, na, Ni, No, A.wq,
+                                                                      A.pstart, A.TW, a.ntot);
+        } else if (ax == 0) {
+            if (last) source_pass_kernel<DF, 1, 1><<<blocks, 256, 0, st>>>(src, dst, total, Qa, na, Ni, No, A.wq, A.pstart, A.TW, a.ntot);
+            else source_pass_kernel<DF, 1, 0><<<blocks, 256, 0, st>>>(src, dst, total, Qa, na, Ni, No, A.wq, A.pstart, A.TW, a.ntot);
+        } else {
+            if (last) source_pass_kernel<DF, 0, 1><<<blocks, 256, 0, st>>>(src, dst, total, Qa, na, Ni, No, A.wq, A.pstart, A.TW, a.ntot);
+            else source_pass_kernel<DF, 0, 0><<<blocks, 256, 0, st>>>(src, dst, total, Qa, na, Ni, No, A.wq, A.pstart, A.TW, a.ntot);
+        }
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        dims_in[ax] = na;
+        src = dst;
+    }
+    return cudaSuccess;
+}
+
+}  // namespace igapw

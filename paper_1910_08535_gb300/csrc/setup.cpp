@@ -1,0 +1,229 @@
+// Host-side set-up of one axis (knots, Gauss rule, PW cells, quadrature points,
+// banded windows).  O(n) work; everything heavier runs on the device.
+#include "setup.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+
+namespace igapw {
+
+static void legendre(int nq, double t, double& pn, double& pn1) {
+    // P_nq(t) and P_{nq-1}(t) by (k+1) P_{k+1} = (2k+1) t P_k - k P_{k-1}
+    double p0 = 1.0, p1 = t;
+    if (nq == 0) { pn = 1.0; pn1 = 0.0; return; }
+    for (int k = 1; k < nq; ++k) {
+        double p2 = ((2.0 * k + 1.0) * t * p1 - k * p0) / (k + 1.0);
+        p0 = p1;
+        p1 = p2;
+    }
+    pn = p1;
+    pn1 = p0;
+}
+
+void gauss_legendre(int nq, std::vector<double>& x, std::vector<double>& w) {
+    // Newton iteration on P_nq; P'_nq(t) = nq (t P_nq - P_{nq-1}) / (t^2 - 1);
+    // weights 2 / ((1 - t^2) P'_nq(t)^2).  Start: t_i ~ cos(pi (i + 3/4) / (nq + 1/2)).
+    x.assign(nq, 0.0);
+    w.assign(nq, 0.0);
+    const double pi = 3.14159265358979323846;
+    for (int i = 0; i < nq; ++i) {
+        double t = std::cos(pi * (i + 0.75) / (nq + 0.5));
+        double pn, pn1, dp;
+        for (int it = 0; it < 100; ++it) {
+            legendre(nq, t, pn, pn1);
+            dp = nq * (t * pn - pn1) / (t * t - 1.0);
+            double step = pn / dp;
+            t -= step;
+            if (std::fabs(step) < 1e-17) break;
+        }
+        legendre(nq, t, pn, pn1);
+        dp = nq * (t * pn - pn1) / (t * t - 1.0);
+        x[i] = t;
+        w[i] = 2.0 / ((1.0 - t * t) * dp * dp);
+    }
+    std::vector<int> idx(nq);
+    for (int i = 0; i < nq; ++i) idx[i] = i;
+    std::sort(idx.begin(), idx.end(), [&](int l, int r) { return x[l] < x[r]; });
+    std::vector<double> xs(nq), ws(nq);
+    for (int i = 0; i < nq; ++i) { xs[i] = x[idx[i]]; ws[i] = w[idx[i]]; }
+    x.swap(xs);
+    w.swap(ws);
+}
+
+static std::string fmt(const char* f, int a, int b = 0) {
+    char buf[256];
+    std::snprintf(buf, sizeof buf, f, a, b);
+    return buf;
+}
+
+std::string build_axis(AxisSetup& ax, int n_elem, int p, int nq, int test, int bc,
+                       const std::vector<double>& knots_in) {
+    ax = AxisSetup();
+    if (p < 2 || p > 4) return fmt("degree %d unsupported (2..4: C^1 or smoother)", p);
+    if (n_elem < 1) return fmt("n_elem %d < 1", n_elem);
+    if (nq < 1 || nq > 16) return fmt("nq %d out of range 1..16", nq);
+    if (test != 0 && test != 1) return fmt("test %d unknown", test);
+    if (bc != 0 && bc != 1) return fmt("bc %d unknown", bc);
+    ax.n_elem = n_elem; ax.p = p; ax.nq = nq; ax.test = test; ax.bc = bc;
+    ax.n = n_elem + p;
+    const int n = ax.n;
+    const int nk = n + p + 1;
+
+    // ---- knots (Sec. 2: open knot vector, n = N_e + p functions) ---------
+    if (knots_in.empty()) {
+        ax.knots.assign(nk, 0.0);
+        for (int k = 0; k < nk; ++k) {
+            int i = k - p;
+            ax.knots[k] = i <= 0 ? 0.0 : (i >= n_elem ? 1.0 : (double)i / n_elem);
+        }
+    } else {
+        if ((int)knots_in.size() != nk)
+            return fmt("knot vector length %d, expected %d", (int)knots_in.size(), nk);
+        ax.knots = knots_in;
+        for (int k = 1; k < nk; ++k)
+            if (!(ax.knots[k] >= ax.knots[k - 1])) return "knot vector not non-decreasing";
+        for (int k = 1; k <= p; ++k)
+            if (ax.knots[k] != ax.knots[0] || ax.knots[nk - 1 - k] != ax.knots[nk - 1])
+                return "knot vector must repeat each end point p+1 times";
+        if (!(ax.knots[nk - 1] > ax.knots[0])) return "empty knot interval";
+        int mult = 0;
+        for (int k = p + 1; k < nk - p - 1; ++k) {
+            mult = (k > p + 1 && ax.knots[k] == ax.knots[k - 1]) ? mult + 1 : 1;
+            if (mult > p - 1) return "interior knot multiplicity > p-1 breaks C^1 continuity";
+            if (ax.knots[k] == ax.knots[0] || ax.knots[k] == ax.knots[nk - 1])
+                return "interior knot equals an end point";
+        }
+    }
+    const double a = ax.knots[0], b = ax.knots[nk - 1];
+    const double tol = 1e-12 * (b - a);
+    ax.brk.clear();
+    for (int k = 0; k < nk; ++k)
+        if (ax.brk.empty() || ax.knots[k] > ax.brk.back()) ax.brk.push_back(ax.knots[k]);
+    const int ne = (int)ax.brk.size() - 1;
+
+    // first non-zero function on element e: s - p with t_s <= brk[e] < t_{s+1}
+    std::vector<int> efirst(ne);
+    for (int e = 0; e < ne; ++e) {
+        int s = 0;
+        for (int k = 0; k < nk - 1; ++k)
+            if (ax.knots[k] <= ax.brk[e] && ax.knots[k + 1] > ax.brk[e]) s = k;
+        efirst[e] = s - p;
+    }
+    auto element_of = [&](double x) {
+        int e = (int)(std::upper_bound(ax.brk.begin(), ax.brk.end(), x) - ax.brk.begin()) - 1;
+        return std::min(std::max(e, 0), ne - 1);
+    };
+
+    // ---- unknowns (Sec. 4.3: Dirichlet rows are replaced) -----------------
+    ax.is_free.assign(n, 1);
+    if (bc == 1) { ax.is_free[0] = 0; ax.is_free[n - 1] = 0; }
+    std::vector<int> unk;
+    for (int i = 0; i < n; ++i) if (ax.is_free[i]) unk.push_back(i);
+    if (unk.empty()) return "no unknowns on an axis";
+
+    std::vector<double> gx, gw;
+    gauss_legendre(nq, gx, gw);
+    auto add_piece = [&](double lo, double hi, int row) {
+        double jac = 0.5 * (hi - lo);
+        int e = element_of(0.5 * (lo + hi));
+        for (int q = 0; q < nq; ++q) {
+            ax.qx.push_back(lo + jac * (gx[q] + 1.0));
+            ax.qw.push_back(jac * gw[q]);
+            ax.qfirst.push_back(efirst[e]);
+            ax.qrow.push_back(row);
+        }
+    };
+
+    ax.pstart.assign(n, 0);
+    ax.pcount.assign(n, 0);
+    if (test == 1) {
+        // ---- PW cells: midpoints of consecutive Greville abscissae --------
+        std::vector<double> xi(n);
+        for (int j = 0; j < n; ++j) {
+            double s = 0.0;
+            for (int k = j + 1; k <= j + p; ++k) s += ax.knots[k];
+            xi[j] = s / p;
+        }
+        ax.cells.push_back(a);
+        for (size_t k = 0; k + 1 < unk.size(); ++k) {
+            double c = 0.5 * (xi[unk[k]] + xi[unk[k + 1]]);
+            for (double kn : ax.brk)
+                if (std::fabs(kn - c) < tol) c = kn;   // snap a knot-coincident midpoint
+            ax.cells.push_back(c);
+        }
+        ax.cells.push_back(b);
+        for (size_t k = 0; k + 1 < ax.cells.size(); ++k)
+            if (!(ax.cells[k + 1] > ax.cells[k])) return "degenerate PW cell";
+        for (size_t k = 0; k < unk.size(); ++k) {
+            int row = unk[k];
+            double lo = ax.cells[k], hi = ax.cells[k + 1];
+            ax.pstart[row] = (int)ax.qx.size();
+            double cur = lo;
+            for (double kn : ax.brk) {
+                if (kn > lo && kn < hi) { add_piece(cur, kn, row); cur = kn; }
+            }
+            add_piece(cur, hi, row);
+            ax.pcount[row] = (int)ax.qx.size() - ax.pstart[row];
+        }
+    } else {
+        // ---- Galerkin: nq Gauss points per element -------------------------
+        std::vector<int> efirst_pt(ne);
+        for (int e = 0; e < ne; ++e) {
+            efirst_pt[e] = (int)ax.qx.size();
+            add_piece(ax.brk[e], ax.brk[e + 1], -1);
+        }
+        for (int i = 0; i < n; ++i) {
+            if (!ax.is_free[i]) continue;
+            // elements where B_i is non-zero: efirst[e] <= i <= efirst[e] + p
+            int e0 = -1, e1 = -1;
+            for (int e = 0; e < ne; ++e)
+                if (efirst[e] <= i && i <= efirst[e] + p) { if (e0 < 0) e0 = e; e1 = e; }
+            if (e0 < 0) return "basis function without support";
+            ax.pstart[i] = efirst_pt[e0];
+            ax.pcount[i] = (e1 - e0 + 1) * nq;
+        }
+    }
+    ax.wq = 0;
+    for (int i = 0; i < n; ++i) ax.wq = std::max(ax.wq, ax.pcount[i]);
+
+    // ---- function windows -----------------------------------------------
+    std::vector<int> lo(n), hi(n);
+    for (int i = 0; i < n; ++i) {
+        if (!ax.is_free[i]) { lo[i] = hi[i] = i; continue; }
+        lo[i] = n; hi[i] = -1;
+        for (int q = ax.pstart[i]; q < ax.pstart[i] + ax.pcount[i]; ++q) {
+            lo[i] = std::min(lo[i], ax.qfirst[q]);
+            hi[i] = std::max(hi[i], ax.qfirst[q] + p);
+        }
+    }
+    ax.w = 0;
+    for (int i = 0; i < n; ++i) ax.w = std::max(ax.w, hi[i] - lo[i] + 1);
+    ax.flo = lo;
+    ax.fhi = hi;
+    for (int i = 0; i < n; ++i) {
+        // the band of the factored system must stay within +-p of the diagonal
+        if (hi[i] - i > p || i - lo[i] > p) return "row couples beyond the +-p band";
+    }
+    if (ax.w > 2 * p + 1) return "window wider than 2p+1";
+    if (!set_window(ax, ax.w))
+        return "knot vector too irregular for the banded layout (row windows must step by 0 or 1)";
+
+    // ---- chunks of the partitioned line solve: P <= 32, length >= p -------
+    ax.P = std::min(32, n / p);
+    if (ax.P < 1) ax.P = 1;
+    for (int k = 0; k <= ax.P; ++k) ax.chunk_b[k] = (int)((long long)k * n / ax.P);
+    return "";
+}
+
+bool set_window(AxisSetup& ax, int wk) {
+    ax.fstart.assign(ax.n, 0);
+    for (int i = 0; i < ax.n; ++i) {
+        ax.fstart[i] = std::max(0, std::min(ax.flo[i], ax.n - wk));
+        if (i > 0 && (ax.fstart[i] < ax.fstart[i - 1] || ax.fstart[i] > ax.fstart[i - 1] + 1)) return false;
+        if (ax.fhi[i] >= ax.fstart[i] + wk) return false;
+    }
+    return true;
+}
+
+}  // namespace igapw

@@ -1,0 +1,282 @@
+"""ctypes binding of libigapw (include/igapw.h): the same call names, argument
+marshalling only.  Every step of the computation runs in the library's CUDA
+kernels; nothing here computes on the host or falls back to a CPU path.
+
+``Context`` wraps a context handle for torch users: it allocates coefficient
+tensors of the layout the library expects and passes their device pointers and
+torch's current CUDA stream.
+"""
+import ctypes
+import os
+import re
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, 'lib', 'libigapw.so')
+HEADER = os.path.join(os.path.dirname(HERE), 'include', 'igapw.h')
+
+# constants mirrored from include/igapw.h (checked against it by the tests)
+IGAPW_OK, IGAPW_ERR_ARG, IGAPW_ERR_SINGULAR, IGAPW_ERR_OOM = 0, -1, -2, -3
+IGAPW_ERR_CUDA, IGAPW_ERR_DEVICE_STATUS, IGAPW_ERR_TIMEOUT = -4, -5, -6
+IGAPW_GALERKIN, IGAPW_PWCONST = 0, 1
+IGAPW_BC_NONE, IGAPW_BC_DIRICHLET0 = 0, 1
+IGAPW_FP64, IGAPW_FP32_REFINE = 0, 1
+IGAPW_OP_MASS, IGAPW_OP_LAPLACE, IGAPW_OP_HEAT, IGAPW_OP_POISSON = 0, 1, 2, 3
+IGAPW_FLAG_DF_RESIDUAL = 1
+
+TESTS = {'galerkin': IGAPW_GALERKIN, 'pw': IGAPW_PWCONST}
+BCS = {'none': IGAPW_BC_NONE, 'dirichlet0': IGAPW_BC_DIRICHLET0}
+PRECISIONS = {'fp64': IGAPW_FP64, 'fp32r': IGAPW_FP32_REFINE}
+OPS = {'mass': IGAPW_OP_MASS, 'laplace': IGAPW_OP_LAPLACE, 'heat': IGAPW_OP_HEAT, 'poisson': IGAPW_OP_POISSON}
+
+
+class IgapwError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f'igapw error {code}: {msg}')
+        self.code = code
+
+
+class igapw_desc(ctypes.Structure):
+    _fields_ = [('dim', ctypes.c_int), ('n_elem', ctypes.c_int * 3), ('degree', ctypes.c_int),
+                ('nq', ctypes.c_int), ('test', ctypes.c_int), ('bc', ctypes.c_int),
+                ('precision', ctypes.c_int), ('op', ctypes.c_int), ('flags', ctypes.c_int)]
+
+
+_VP, _I, _D = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+_SIGS = {
+    'igapw_create': (_I, [ctypes.POINTER(_VP), ctypes.POINTER(igapw_desc), _VP]),
+    'igapw_set_knots': (_I, [_VP, _I, ctypes.POINTER(_D), _I]),
+    'igapw_quad_points': (_I, [_VP, _I, ctypes.POINTER(_D), ctypes.POINTER(_D), ctypes.POINTER(_I)]),
+    'igapw_basis_table': (_I, [_VP, _I, ctypes.POINTER(_D), ctypes.POINTER(_I)]),
+    'igapw_rhs_source': (_I, [_VP, _VP, _VP]),
+    'igapw_apply': (_I, [_VP, _I, _D, _VP, _VP]),
+    'igapw_assemble_1d': (_I, [_VP, _I, _I, ctypes.POINTER(_D)]),
+    'igapw_solve': (_I, [_VP, _VP, _VP]),
+    'igapw_step': (_I, [_VP, _D, _I, _VP]),
+    'igapw_step_host': (_I, [_VP, _D, _I, _VP]),
+    'igapw_sync_status': (_I, [_VP]),
+    'igapw_last_error': (ctypes.c_char_p, [_VP]),
+    'igapw_size': (ctypes.c_longlong, [_VP, ctypes.POINTER(_I)]),
+    'igapw_destroy': (_I, [_VP]),
+}
+
+_lib = None
+
+
+def header_symbols(path=HEADER):
+    """Names of the functions declared in include/igapw.h."""
+    txt = open(path).read()
+    return sorted(set(re.findall(r'^\s*(?:int|long long|const char\*)\s+(igapw_\w+)\s*\(', txt, re.M)))
+
+
+def load(path=LIB_PATH):
+    """Load libigapw.so (no CUDA context is created).  Raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f'libigapw.so not built at {path}: run paper_1910_08535_gb300/_build.py '
+                           '(there is no CPU fallback)')
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(rc, ctx=None):
+    if rc != IGAPW_OK:
+        msg = load().igapw_last_error(ctx)
+        raise IgapwError(rc, msg.decode() if msg else '')
+
+
+def _dptr(a):
+    return ctypes.cast(ctypes.c_void_p(a.data_ptr() if hasattr(a, 'data_ptr') else int(a)), ctypes.c_void_p)
+
+
+def _stream_handle(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    return ctypes.c_void_p(stream.cuda_stream if hasattr(stream, 'cuda_stream') else int(stream))
+
+
+# ---- the C ABI, same names -------------------------------------------------
+
+def igapw_create(desc, stream=None):
+    ctx = ctypes.c_void_p()
+    rc = load().igapw_create(ctypes.byref(ctx), ctypes.byref(desc), _stream_handle(stream))
+    _check(rc, None)
+    return ctx
+
+
+def igapw_set_knots(ctx, axis, knots):
+    import numpy as np
+    k = np.ascontiguousarray(knots, dtype=np.float64)
+    _check(load().igapw_set_knots(ctx, axis, k.ctypes.data_as(ctypes.POINTER(_D)), len(k)), ctx)
+
+
+def igapw_quad_points(ctx, axis):
+    import numpy as np
+    cnt = _I()
+    _check(load().igapw_quad_points(ctx, axis, None, None, ctypes.byref(cnt)), ctx)
+    x = np.empty(cnt.value)
+    w = np.empty(cnt.value)
+    _check(load().igapw_quad_points(ctx, axis, x.ctypes.data_as(ctypes.POINTER(_D)),
+                                    w.ctypes.data_as(ctypes.POINTER(_D)), ctypes.byref(cnt)), ctx)
+    return x, w
+
+
+def igapw_basis_table(ctx, axis, p):
+    import numpy as np
+    x, _ = igapw_quad_points(ctx, axis)
+    vals = np.empty((len(x), p + 1, 3))
+    first = np.empty(len(x), dtype=np.int32)
+    _check(load().igapw_basis_table(ctx, axis, vals.ctypes.data_as(ctypes.POINTER(_D)),
+                                    first.ctypes.data_as(ctypes.POINTER(_I))), ctx)
+    return vals, first
+
+
+def igapw_rhs_source(ctx, f, b):
+    _check(load().igapw_rhs_source(ctx, _dptr(f), _dptr(b)), ctx)
+
+
+def igapw_apply(ctx, op, dt, u, r):
+    _check(load().igapw_apply(ctx, op, float(dt), _dptr(u), _dptr(r)), ctx)
+
+
+def igapw_assemble_1d(ctx, axis, which, n):
+    import numpy as np
+    out = np.empty((n, n))
+    _check(load().igapw_assemble_1d(ctx, axis, which, out.ctypes.data_as(ctypes.POINTER(_D))), ctx)
+    return out
+
+
+def igapw_solve(ctx, r, u):
+    _check(load().igapw_solve(ctx, _dptr(r), _dptr(u)), ctx)
+
+
+def igapw_step(ctx, dt, nsteps, u):
+    _check(load().igapw_step(ctx, float(dt), int(nsteps), _dptr(u)), ctx)
+
+
+def igapw_step_host(ctx, dt, nsteps, u_host):
+    _check(load().igapw_step_host(ctx, float(dt), int(nsteps), _dptr(u_host)), ctx)
+
+
+def igapw_sync_status(ctx):
+    _check(load().igapw_sync_status(ctx), ctx)
+
+
+def igapw_last_error(ctx):
+    return load().igapw_last_error(ctx).decode()
+
+
+def igapw_size(ctx):
+    dims = (_I * 3)()
+    n = load().igapw_size(ctx, dims)
+    return n, tuple(dims)
+
+
+def igapw_destroy(ctx):
+    _check(load().igapw_destroy(ctx), None)
+
+
+# ---- torch convenience wrapper ----------------------------------------------
+
+class Context:
+    """One problem instance.  Coefficient tensors: float64 of shape
+    (n_z, n_y, n_x)[-dim:] for precision 'fp64'; float32 of shape
+    (2, n_z, n_y, n_x)[...] (hi plane, lo plane) for 'fp32r'."""
+
+    def __init__(self, dim, n_elem, degree, nq, test='pw', bc='none', precision='fp64', op='heat',
+                 flags=0, stream=None):
+        import torch
+        if isinstance(n_elem, int):
+            n_elem = [n_elem] * dim
+        d = igapw_desc()
+        d.dim = dim
+        for a in range(3):
+            d.n_elem[a] = n_elem[a] if a < dim else 1
+        d.degree, d.nq = degree, nq
+        d.test, d.bc = TESTS[test], BCS[bc]
+        d.precision, d.op, d.flags = PRECISIONS[precision], OPS[op], flags
+        self.desc = d
+        self.dim, self.p, self.precision = dim, degree, precision
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.ctx = igapw_create(d, self.stream)
+        self.ntot, dims = igapw_size(self.ctx)
+        self.n = dims                                   # (n_x, n_y, n_z)
+        self.shape = tuple(reversed(dims[:dim]))        # (n_z, n_y, n_x)[-dim:]
+
+    # tensors --------------------------------------------------------------
+    def empty(self):
+        import torch
+        if self.precision == 'fp64':
+            return torch.empty(self.shape, dtype=torch.float64, device='cuda')
+        return torch.empty((2,) + self.shape, dtype=torch.float32, device='cuda')
+
+    def from_numpy(self, u):
+        """Device coefficient tensor from a float64 array (split into hi/lo for fp32r)."""
+        import numpy as np
+        import torch
+        u = np.ascontiguousarray(u, dtype=np.float64).reshape(self.shape)
+        if self.precision == 'fp64':
+            return torch.from_numpy(u).cuda()
+        hi = u.astype(np.float32)
+        lo = (u - hi.astype(np.float64)).astype(np.float32)
+        return torch.from_numpy(np.stack([hi, lo])).cuda()
+
+    def to_numpy(self, t):
+        import numpy as np
+        a = t.detach().cpu().numpy()
+        if self.precision == 'fp64':
+            return a.astype(np.float64)
+        return a[0].astype(np.float64) + a[1].astype(np.float64)
+
+    # calls -------------------------------------------------------------------
+    def apply(self, op, u, dt=0.0, out=None):
+        out = self.empty() if out is None else out
+        igapw_apply(self.ctx, OPS[op], dt, u, out)
+        return out
+
+    def solve(self, r, out=None):
+        out = self.empty() if out is None else out
+        igapw_solve(self.ctx, r, out)
+        return out
+
+    def step(self, u, dt, nsteps):
+        igapw_step(self.ctx, dt, nsteps, u)
+        return u
+
+    def rhs_source(self, f, out=None):
+        out = self.empty() if out is None else out
+        igapw_rhs_source(self.ctx, f, out)
+        return out
+
+    def quad_points(self, axis):
+        return igapw_quad_points(self.ctx, axis)
+
+    def basis_table(self, axis):
+        return igapw_basis_table(self.ctx, axis, self.p)
+
+    def assemble_1d(self, axis, which):
+        return igapw_assemble_1d(self.ctx, axis, OPS[which], self.n[axis])
+
+    def set_knots(self, axis, knots):
+        igapw_set_knots(self.ctx, axis, knots)
+
+    def sync(self):
+        igapw_sync_status(self.ctx)
+
+    def close(self):
+        if self.ctx:
+            igapw_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

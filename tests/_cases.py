@@ -1,0 +1,25 @@
+"""Shared helpers for the GPU parity tests: build the oracle's axes for a
+library context and compare arrays."""
+import numpy as np
+
+from oracle import systems
+
+
+def oracle_axes(dim, n_elem, p, nq, test, bc='none'):
+    if isinstance(n_elem, int):
+        n_elem = [n_elem] * dim
+    return [systems.Axis(n_elem[a], p, nq, test, bc) for a in range(dim)]
+
+
+def rel_l2(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def max_abs(a, b):
+    return float(np.max(np.abs(np.asarray(a, dtype=np.float64) - np.asarray(b, dtype=np.float64))))
+
+
+# tolerances (relative L2) stated for the two precisions
+TOL = {'fp64': 1e-12, 'fp32r': 1e-5}

@@ -1,0 +1,54 @@
+"""The C-ABI library builds for sm_103a, loads without a GPU, and exports every
+function include/igapw.h declares; the binding's constants match the header."""
+import re
+
+import pytest
+
+
+@pytest.fixture(scope='module')
+def lib():
+    from paper_1910_08535_gb300 import _build, igapw
+    _build.build()
+    return igapw.load()
+
+
+def test_exports_every_declared_symbol(lib):
+    from paper_1910_08535_gb300 import igapw
+    names = igapw.header_symbols()
+    assert len(names) >= 14
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+    assert set(names) == set(igapw._SIGS), set(names) ^ set(igapw._SIGS)
+
+
+def test_constants_match_header():
+    from paper_1910_08535_gb300 import igapw
+    txt = open(igapw.HEADER).read()
+    defs = dict((m[0], int(m[1])) for m in re.findall(r'#define\s+(IGAPW_\w+)\s+(-?\d+)', txt))
+    for name, val in defs.items():
+        if hasattr(igapw, name):
+            assert getattr(igapw, name) == val, name
+    for name in ('IGAPW_PWCONST', 'IGAPW_FP32_REFINE', 'IGAPW_OP_POISSON', 'IGAPW_ERR_SINGULAR'):
+        assert name in defs and hasattr(igapw, name)
+
+
+def test_desc_layout_matches_header():
+    """igapw_desc is nine ints in the header's order."""
+    from paper_1910_08535_gb300 import igapw
+    txt = open(igapw.HEADER).read()
+    body = re.search(r'typedef struct \{(.*?)\} igapw_desc;', txt, re.S).group(1)
+    fields = re.findall(r'int\s+(\w+)(?:\[(\d)\])?;', body)
+    assert [f[0] for f in fields] == [f[0] for f in igapw.igapw_desc._fields_]
+    import ctypes
+    assert ctypes.sizeof(igapw.igapw_desc) == 11 * 4
+
+
+def test_missing_library_fails_loudly(tmp_path):
+    from paper_1910_08535_gb300 import igapw
+    saved = igapw._lib
+    try:
+        igapw._lib = None
+        with pytest.raises(RuntimeError, match='not built'):
+            igapw.load(str(tmp_path / 'nope.so'))
+    finally:
+        igapw._lib = saved
