@@ -35,7 +35,8 @@
  *     of 2 * n_total elements whose value is hi + lo.  Contractions run in FP32
  *     with error-free products and two-sum accumulation; line solves run in
  *     FP32 with one step of iterative refinement whose residual is formed in
- *     FP64 (or in double-float, IGAPW_FLAG_DF_RESIDUAL).  Quadrature-point
+ *     double-float (or in FP64 with IGAPW_FLAG_FP64_RESIDUAL; GB300 runs FP64
+ *     at 1/58 of its FP32 rate, so double-float is the default).  Quadrature-point
  *     samples f passed to igapw_rhs_source are plain float in this mode.
  *   - Work is enqueued on the CUDA stream given at create time and is
  *     asynchronous; calls do not synchronize unless stated.
@@ -72,8 +73,8 @@ extern "C" {
 #define IGAPW_OP_HEAT       2  /* F u = u + dt Lap u (explicit step, Sec. 4.2)      */
 #define IGAPW_OP_POISSON    3  /* F u = -Lap u    (1D Poisson system, Sec. 4.3)     */
 
-#define IGAPW_FLAG_DF_RESIDUAL 1  /* FP32_REFINE: refinement residual in double-float
-                                     (FP32 pairs) instead of FP64                    */
+#define IGAPW_FLAG_FP64_RESIDUAL 1  /* FP32_REFINE: form the refinement residual in FP64
+                                       instead of double-float (FP32 pairs)           */
 
 #define IGAPW_MAX_DIM    3
 #define IGAPW_MAX_DEGREE 4
@@ -155,7 +156,7 @@ int igapw_assemble_1d(igapw_ctx* ctx, int axis, int which, double* dense_host);
 /* Solves S u = r with S the tensor product of the per-axis system matrices
  * (mass, or the 1D Poisson operator): one batch of banded line solves per
  * axis with the precomputed FP64 LU factors [Sec. 4.1 ADS].  FP32_REFINE: an
- * FP32 solve, the residual r - S u0 (FP64 or double-float), a second FP32
+ * FP32 solve, the residual r - S u0 (double-float or FP64), a second FP32
  * solve, u = u0 + correction stored as a hi/lo pair.  r_dev == u_dev is
  * allowed. Asynchronous. */
 int igapw_solve(igapw_ctx* ctx, const void* r_dev, void* u_dev);

@@ -19,8 +19,7 @@ struct AxisMem {
     double *knots = nullptr, *qx = nullptr, *qw = nullptr, *vals = nullptr;
     int *qfirst = nullptr, *fstart = nullptr, *pstart = nullptr, *pcount = nullptr, *is_free = nullptr;
     double *A = nullptr, *C = nullptr, *S = nullptr, *TW = nullptr;
-    float *Ahi = nullptr, *Alo = nullptr, *Chi = nullptr, *Clo = nullptr, *Shi = nullptr, *Slo = nullptr;
-    float *TWhi = nullptr, *TWlo = nullptr;
+    float2 *Adf = nullptr, *Cdf = nullptr, *Sdf = nullptr, *TWdf = nullptr;
     double *band = nullptr, *L = nullptr, *U = nullptr, *dinv = nullptr, *G = nullptr, *H = nullptr,
            *PhiF = nullptr, *PhiB = nullptr;
     float *L32 = nullptr, *U32 = nullptr, *dinv32 = nullptr, *G32 = nullptr, *H32 = nullptr,
@@ -125,10 +124,8 @@ int build_axis_device(igapw_ctx* c, int a) {
     const size_t nw = (size_t)n * W, nt = (size_t)n * WQ;
     CKC(c, dalloc(c, &m.A, nw)); CKC(c, dalloc(c, &m.C, nw)); CKC(c, dalloc(c, &m.S, nw));
     CKC(c, dalloc(c, &m.TW, nt));
-    CKC(c, dalloc(c, &m.Ahi, nw)); CKC(c, dalloc(c, &m.Alo, nw));
-    CKC(c, dalloc(c, &m.Chi, nw)); CKC(c, dalloc(c, &m.Clo, nw));
-    CKC(c, dalloc(c, &m.Shi, nw)); CKC(c, dalloc(c, &m.Slo, nw));
-    CKC(c, dalloc(c, &m.TWhi, nt)); CKC(c, dalloc(c, &m.TWlo, nt));
+    CKC(c, dalloc(c, &m.Adf, nw)); CKC(c, dalloc(c, &m.Cdf, nw)); CKC(c, dalloc(c, &m.Sdf, nw));
+    CKC(c, dalloc(c, &m.TWdf, nt));
     const size_t np = (size_t)n * p, nphi = (size_t)5 * 32 * p * p;
     CKC(c, dalloc(c, &m.band, (size_t)n * (2 * p + 1)));
     CKC(c, dalloc(c, &m.L, np)); CKC(c, dalloc(c, &m.U, np)); CKC(c, dalloc(c, &m.dinv, (size_t)n));
@@ -145,8 +142,7 @@ int build_axis_device(igapw_ctx* c, int a) {
     f.fstart = m.fstart; f.pstart = m.pstart; f.pcount = m.pcount; f.is_free = m.is_free;
     f.qfirst = m.qfirst; f.qw = m.qw; f.vals = m.vals;
     f.A = m.A; f.C = m.C; f.S = m.S; f.TW = m.TW;
-    f.Ahi = m.Ahi; f.Alo = m.Alo; f.Chi = m.Chi; f.Clo = m.Clo; f.Shi = m.Shi; f.Slo = m.Slo;
-    f.TWhi = m.TWhi; f.TWlo = m.TWlo;
+    f.Adf = m.Adf; f.Cdf = m.Cdf; f.Sdf = m.Sdf; f.TWdf = m.TWdf;
     launch_fold(f, c->stream);
     // kernel (c1): FP64 banded LU + partitioned-solve data
     FactorArgs fa{};
@@ -163,10 +159,10 @@ int build_axis_device(igapw_ctx* c, int a) {
     AxisDev& D = c->dev[a];
     D.n = n; D.nq = Q; D.wq = WQ;
     D.fstart = m.fstart; D.pstart = m.pstart; D.is_free = m.is_free;
-    D.A = {m.A, m.Ahi, m.Alo};
-    D.C = {m.C, m.Chi, m.Clo};
-    D.S = {m.S, m.Shi, m.Slo};
-    D.TW = {m.TW, m.TWhi, m.TWlo};
+    D.A = {m.A, m.Adf};
+    D.C = {m.C, m.Cdf};
+    D.S = {m.S, m.Sdf};
+    D.TW = {m.TW, m.TWdf};
     D.ls64.n = n; D.ls64.P = s.P;
     D.ls32.n = n; D.ls32.P = s.P;
     for (int k = 0; k < 33; ++k) { D.ls64.b[k] = s.chunk_b[k]; D.ls32.b[k] = s.chunk_b[k]; }
@@ -240,7 +236,7 @@ int enqueue_solve(igapw_ctx* c, const void* r, void* u, cudaStream_t st) {
     a.u = c->u0;
     a.r = r;
     a.out = c->rho;
-    const int cmp = (c->d.flags & IGAPW_FLAG_DF_RESIDUAL) ? FMT_PAIR : FMT_F64;
+    const int cmp = (c->d.flags & IGAPW_FLAG_FP64_RESIDUAL) ? FMT_F64 : FMT_PAIR;
     cudaError_t e = launch_contract(a, MODE_RES, cmp, FMT_PAIR, st);
     if (e != cudaSuccess) return fail(c, IGAPW_ERR_CUDA, std::string("residual: ") + cudaGetErrorString(e));
     return solve_chain(c, c->rho, FMT_F32, u, FMT_PAIR, c->u0, st);
@@ -318,6 +314,7 @@ int setup_all(igapw_ctx* c, const std::vector<double>* knots_override, int overr
     if (c->W < 0) return fail(c, IGAPW_ERR_ARG, "window too wide");
     for (int a = 0; a < c->dim; ++a)
         if (!set_window(c->ax[a], c->W)) return fail(c, IGAPW_ERR_ARG, "banded window layout failed");
+    for (int a = 0; a < c->dim; ++a) set_chunks(c->ax[a], c->ntot / c->n[a]);
     for (int a = 0; a < c->dim; ++a) {
         int rc = build_axis_device(c, a);
         if (rc) return rc;
@@ -400,6 +397,7 @@ int igapw_set_knots(igapw_ctx* c, int axis, const double* knots, int len) {
     if (c->W < 0) return fail(c, IGAPW_ERR_ARG, "window too wide");
     for (int a = 0; a < c->dim; ++a)
         if (!set_window(c->ax[a], c->W)) return fail(c, IGAPW_ERR_ARG, "banded window layout failed");
+    for (int a = 0; a < c->dim; ++a) set_chunks(c->ax[a], c->ntot / c->n[a]);
     for (int a = 0; a < c->dim; ++a) {
         int rc = build_axis_device(c, a);
         if (rc) return rc;

@@ -86,9 +86,8 @@ __host__ __device__ inline void split_double(double v, float& hi, float& lo) {
 // [fstart[i], fstart[i] + W) with W the padded kernel width of the context.
 // ---------------------------------------------------------------------------
 struct TableSet {
-    const double* d;   // FP64 [n * W]
-    const float* hi;   // FP32 pair hi [n * W]
-    const float* lo;   // FP32 pair lo [n * W]
+    const double* d;    // FP64 [n * W]
+    const float2* df;   // double-float (hi, lo) interleaved [n * W]
 };
 
 // Precomputed data of the partitioned banded solve of one 1D system

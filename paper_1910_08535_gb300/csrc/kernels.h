@@ -18,7 +18,7 @@ struct FoldArgs {
     const double* qw;
     const double* vals;
     double *A, *C, *S, *TW;
-    float *Ahi, *Alo, *Chi, *Clo, *Shi, *Slo, *TWhi, *TWlo;
+    float2 *Adf, *Cdf, *Sdf, *TWdf;
 };
 
 struct FactorArgs {
@@ -49,6 +49,7 @@ struct ContractArgs {
     int dim, W;
     int n[3];               // n_x, n_y, n_z
     int zchunk;
+    int tx, ty;             // runtime tile widths (<= the kernel's compile-time tile)
     AxisDev ax[3];
     const void* u;          // MODE_OP/SYS: F64 or PAIR; MODE_RES: F32 u0
     const void* r;          // MODE_RES: PAIR right-hand side

@@ -52,14 +52,15 @@ struct SBuf<double> {
 };
 template <>
 struct SBuf<DF> {
-    float* h;
-    float* l;
-    __device__ __forceinline__ DF ld(int i) const { return DF{h[i], l[i]}; }
-    __device__ __forceinline__ void st(int i, DF v) const { h[i] = v.hi; l[i] = v.lo; }
+    float2* p;   // (hi, lo) interleaved: one 8-byte access per value
+    __device__ __forceinline__ DF ld(int i) const {
+        const float2 v = p[i];
+        return DF{v.x, v.y};
+    }
+    __device__ __forceinline__ void st(int i, DF v) const { p[i] = make_float2(v.hi, v.lo); }
     static constexpr int bytes = 8;
     __device__ __forceinline__ void carve(unsigned char*& base, int count) {
-        h = reinterpret_cast<float*>(base);
-        l = h + count;
+        p = reinterpret_cast<float2*>(base);
         base += (size_t)count * 8;
     }
 };
@@ -69,7 +70,10 @@ __device__ __forceinline__ CT tab(const TableSet& t, int idx);
 template <>
 __device__ __forceinline__ double tab<double>(const TableSet& t, int idx) { return __ldg(t.d + idx); }
 template <>
-__device__ __forceinline__ DF tab<DF>(const TableSet& t, int idx) { return DF{__ldg(t.hi + idx), __ldg(t.lo + idx)}; }
+__device__ __forceinline__ DF tab<DF>(const TableSet& t, int idx) {
+    const float2 v = __ldg(t.df + idx);
+    return DF{v.x, v.y};
+}
 
 template <typename CT>
 __device__ __forceinline__ CT zero_v();
@@ -126,6 +130,26 @@ __device__ __forceinline__ void store_r(const ContractArgs& a, long long g, CT v
     }
 }
 
+// Row/column iteration over a rows x cols tile with a fixed thread stride,
+// without an integer division per element.
+struct Iter2 {
+    int r, c, dr, dc, cols;
+    __device__ __forceinline__ Iter2(int cols_, int start, int stride) : cols(cols_) {
+        r = start / cols;
+        c = start - r * cols;
+        dr = stride / cols;
+        dc = stride - dr * cols;
+    }
+    __device__ __forceinline__ void next() {
+        c += dc;
+        r += dr;
+        if (c >= cols) {
+            c -= cols;
+            ++r;
+        }
+    }
+};
+
 template <int DIM, int W, int TX, int TY, typename CT, int MODE, int IO>
 __global__ void __launch_bounds__(256) contract_kernel(const ContractArgs a) {
     constexpr bool OP = (MODE == MODE_OP);
@@ -138,10 +162,10 @@ __global__ void __launch_bounds__(256) contract_kernel(const ContractArgs a) {
     const AxisDev& AX = a.ax[0];
     const AxisDev& AY = a.ax[1];
     const AxisDev& AZ = a.ax[2];
-    const int x0 = blockIdx.x * TX;
-    const int y0 = DIM >= 2 ? blockIdx.y * TY : 0;
-    const int nxo = min(TX, nx - x0);
-    const int nyo = DIM >= 2 ? min(TY, ny - y0) : 1;
+    const int x0 = blockIdx.x * a.tx;
+    const int y0 = DIM >= 2 ? blockIdx.y * a.ty : 0;
+    const int nxo = min(a.tx, nx - x0);
+    const int nyo = DIM >= 2 ? min(a.ty, ny - y0) : 1;
     const int xl = AX.fstart[x0];
     const int nxh = AX.fstart[x0 + nxo - 1] + W - xl;
     const int yl = DIM >= 2 ? AY.fstart[y0] : 0;
@@ -164,8 +188,8 @@ __global__ void __launch_bounds__(256) contract_kernel(const ContractArgs a) {
 
     // x-pass over the y-rows of Q1/Q2 for output plane zo, then store
     auto x_pass = [&](int zo) {
-        for (int e = threadIdx.x; e < nyo * nxo; e += blockDim.x) {
-            const int y = e / nxo, x = e - y * nxo;
+        for (Iter2 it(nxo, threadIdx.x, blockDim.x); it.r < nyo; it.next()) {
+            const int y = it.r, x = it.c;
             const int xc = x0 + x;
             const int sx = AX.fstart[xc] - xl;
             const int qb = y * XH + sx;
@@ -198,8 +222,8 @@ __global__ void __launch_bounds__(256) contract_kernel(const ContractArgs a) {
 
     // y-pass: ZA (and ZC) rows -> Q1 (and Q2)
     auto y_pass = [&]() {
-        for (int e = threadIdx.x; e < nyo * nxh; e += blockDim.x) {
-            const int y = e / nxh, xx = e - y * nxh;
+        for (Iter2 it(nxh, threadIdx.x, blockDim.x); it.r < nyo; it.next()) {
+            const int y = it.r, xx = it.c;
             const int yr = y0 + y;
             const int sy = AY.fstart[yr] - yl;
             Acc<CT> q1;
@@ -210,9 +234,10 @@ __global__ void __launch_bounds__(256) contract_kernel(const ContractArgs a) {
 #pragma unroll
                 for (int w = 0; w < W; ++w) {
                     const CT za = ZA.ld((sy + w) * XH + xx);
-                    q1.add_prod(tab<CT>(AY.A, yr * W + w), za);
+                    const CT ta = tab<CT>(AY.A, yr * W + w);
+                    q1.add_prod(ta, za);
                     t2.add_prod(tab<CT>(AY.C, yr * W + w), za);
-                    if constexpr (DIM == 3) t2.add_prod(tab<CT>(AY.A, yr * W + w), ZC.ld((sy + w) * XH + xx));
+                    if constexpr (DIM == 3) t2.add_prod(ta, ZC.ld((sy + w) * XH + xx));
                 }
                 const CT v1 = q1.result();
                 Acc<CT> q2;
@@ -244,10 +269,9 @@ __global__ void __launch_bounds__(256) contract_kernel(const ContractArgs a) {
         __syncthreads();
         x_pass(0);
     } else if constexpr (DIM == 2) {
-        for (int e = threadIdx.x; e < nyh * nxh; e += blockDim.x) {
-            const int yy = e / nxh, xx = e - yy * nxh;
-            const int gy = yl + yy, gx = xl + xx;
-            ZA.st(yy * XH + xx, (gy < ny && gx < nx) ? load_u<CT, MODE, IO>(a, (long long)gy * nx + gx) : zero_v<CT>());
+        for (Iter2 it(nxh, threadIdx.x, blockDim.x); it.r < nyh; it.next()) {
+            const int gy = yl + it.r, gx = xl + it.c;
+            ZA.st(it.r * XH + it.c, (gy < ny && gx < nx) ? load_u<CT, MODE, IO>(a, (long long)gy * nx + gx) : zero_v<CT>());
         }
         __syncthreads();
         y_pass();
@@ -256,39 +280,80 @@ __global__ void __launch_bounds__(256) contract_kernel(const ContractArgs a) {
     } else {
         const int z0 = blockIdx.z * a.zchunk;
         const int z1 = min(z0 + a.zchunk, nz);
+        // this thread's elements of a halo plane: e = threadIdx.x + k * 256
+        constexpr int PF = (YH * XH + 255) / 256;
+        int poff[PF];        // ring offset (row * XH + col), -1 if none
+        long long pg[PF];    // global offset within a z-plane, -1 if outside the tensor
+        {
+            Iter2 it(nxh, threadIdx.x, 256);
+#pragma unroll
+            for (int k = 0; k < PF; ++k) {
+                const bool in = it.r < nyh;
+                const int gy = yl + it.r, gx = xl + it.c;
+                poff[k] = in ? it.r * XH + it.c : -1;
+                pg[k] = (in && gy < ny && gx < nx) ? (long long)gy * nx + gx : -1;
+                it.next();
+            }
+        }
+        auto plane_val = [&](int z, int k) {
+            CT v = zero_v<CT>();
+            if (z < nz && pg[k] >= 0) v = load_u<CT, MODE, IO>(a, (long long)z * plane + pg[k]);
+            return v;
+        };
+        // register prefetch of the plane the next output plane needs, issued
+        // before this plane's z-pass and committed to the ring after it
+        CT pf[PF];
         int rhi = AZ.fstart[z0];
         for (int zo = z0; zo < z1; ++zo) {
             const int zs = AZ.fstart[zo];
-            while (rhi < zs + W) {
+            while (rhi < zs + W) {          // fill (first plane of the chunk only)
                 const int slot = (rhi % W) * (YH * XH);
-                for (int e = threadIdx.x; e < nyh * nxh; e += blockDim.x) {
-                    const int yy = e / nxh, xx = e - yy * nxh;
-                    const int gy = yl + yy, gx = xl + xx;
-                    CT v = zero_v<CT>();
-                    if (rhi < nz && gy < ny && gx < nx)
-                        v = load_u<CT, MODE, IO>(a, (long long)rhi * plane + (long long)gy * nx + gx);
-                    ring.st(slot + yy * XH + xx, v);
-                }
+#pragma unroll
+                for (int k = 0; k < PF; ++k) pf[k] = plane_val(rhi, k);
+#pragma unroll
+                for (int k = 0; k < PF; ++k)
+                    if (poff[k] >= 0) ring.st(slot + poff[k], pf[k]);
                 ++rhi;
             }
+            const bool pre = (zo + 1 < z1) && (AZ.fstart[zo + 1] + W > rhi);
+            if (pre) {
+#pragma unroll
+                for (int k = 0; k < PF; ++k) pf[k] = plane_val(rhi, k);
+            }
+            // this plane's z tables, uniform over the block
+            CT tza[W], tzc[W];
+#pragma unroll
+            for (int w = 0; w < W; ++w) {
+                tza[w] = tab<CT>(TZa, zo * W + w);
+                if constexpr (OP) tzc[w] = tab<CT>(AZ.C, zo * W + w);
+            }
+            int slot_w[W];
+#pragma unroll
+            for (int w = 0; w < W; ++w) slot_w[w] = ((zs + w) % W) * (YH * XH);
             __syncthreads();
             // z-pass
-            for (int e = threadIdx.x; e < nyh * nxh; e += blockDim.x) {
-                const int yy = e / nxh, xx = e - yy * nxh;
-                const int off = yy * XH + xx;
+            for (Iter2 it(nxh, threadIdx.x, blockDim.x); it.r < nyh; it.next()) {
+                const int off = it.r * XH + it.c;
                 Acc<CT> za, zc;
                 za.init();
                 zc.init();
 #pragma unroll
                 for (int w = 0; w < W; ++w) {
-                    const CT v = ring.ld(((zs + w) % W) * (YH * XH) + off);
-                    za.add_prod(tab<CT>(TZa, zo * W + w), v);
-                    if constexpr (OP) zc.add_prod(tab<CT>(AZ.C, zo * W + w), v);
+                    const CT v = ring.ld(slot_w[w] + off);
+                    za.add_prod(tza[w], v);
+                    if constexpr (OP) zc.add_prod(tzc[w], v);
                 }
                 ZA.st(off, za.result());
                 if constexpr (OP) ZC.st(off, zc.result());
             }
             __syncthreads();
+            if (pre) {                      // slot of plane zs is free now
+                const int slot = (rhi % W) * (YH * XH);
+#pragma unroll
+                for (int k = 0; k < PF; ++k)
+                    if (poff[k] >= 0) ring.st(slot + poff[k], pf[k]);
+                ++rhi;
+            }
             y_pass();
             __syncthreads();
             x_pass(zo);
@@ -314,9 +379,24 @@ static cudaError_t run_contract(const ContractArgs& a, cudaStream_t st) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e != cudaSuccess) return e;
     }
-    dim3 grid((a.n[0] + TX - 1) / TX, DIM >= 2 ? (a.n[1] + TY - 1) / TY : 1,
-              DIM == 3 ? (a.n[2] + a.zchunk - 1) / a.zchunk : 1);
-    k<<<grid, 256, sm, st>>>(a);
+    // balanced runtime tiles: the fewest tiles of at most TX (TY), evenly sized
+    ContractArgs b = a;
+    const int ntx = (a.n[0] + TX - 1) / TX;
+    b.tx = (a.n[0] + ntx - 1) / ntx;
+    const int nty = DIM >= 2 ? (a.n[1] + TY - 1) / TY : 1;
+    b.ty = DIM >= 2 ? (a.n[1] + nty - 1) / nty : 1;
+    int nz_blocks = 1;
+    if (DIM == 3) {
+        // z-chunks: about 4 resident blocks per SM over the grid
+        const long long want = 4LL * 152;
+        long long chunks = (want + (long long)ntx * nty - 1) / ((long long)ntx * nty);
+        if (chunks < 1) chunks = 1;
+        b.zchunk = (int)((a.n[2] + chunks - 1) / chunks);
+        if (b.zchunk < 4) b.zchunk = 4;
+        nz_blocks = (a.n[2] + b.zchunk - 1) / b.zchunk;
+    }
+    dim3 grid((a.n[0] + b.tx - 1) / b.tx, DIM >= 2 ? (a.n[1] + b.ty - 1) / b.ty : 1, nz_blocks);
+    k<<<grid, 256, sm, st>>>(b);
     return cudaGetLastError();
 }
 
@@ -324,7 +404,7 @@ template <int DIM, int W, typename CT, int MODE, int IO>
 static cudaError_t pick_tile(const ContractArgs& a, cudaStream_t st) {
     if constexpr (DIM == 1) return run_contract<1, W, 256, 1, CT, MODE, IO>(a, st);
     else if constexpr (DIM == 2) return run_contract<2, W, 64, 8, CT, MODE, IO>(a, st);
-    else return run_contract<3, W, 32, 8, CT, MODE, IO>(a, st);
+    else return run_contract<3, W, 48, 8, CT, MODE, IO>(a, st);
 }
 
 template <int DIM, int W>

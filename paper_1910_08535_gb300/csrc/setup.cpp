@@ -210,10 +210,19 @@ std::string build_axis(AxisSetup& ax, int n_elem, int p, int nq, int test, int b
         return "knot vector too irregular for the banded layout (row windows must step by 0 or 1)";
 
     // ---- chunks of the partitioned line solve: P <= 32, length >= p -------
-    ax.P = std::min(32, n / p);
-    if (ax.P < 1) ax.P = 1;
-    for (int k = 0; k <= ax.P; ++k) ax.chunk_b[k] = (int)((long long)k * n / ax.P);
+    set_chunks(ax, 1);
     return "";
+}
+
+void set_chunks(AxisSetup& ax, long long lines) {
+    // P a power of two <= 32 (the lane group of a warp that shares a line):
+    // the smallest one whose chunks fit the register-resident solve
+    // (ceil(n / P) <= 20 rows), never with chunks shorter than p rows.
+    (void)lines;
+    const int n = ax.n, p = ax.p;
+    ax.P = 1;
+    while (ax.P < 32 && (n + ax.P - 1) / ax.P > 20 && n / (2 * ax.P) >= p) ax.P *= 2;
+    for (int k = 0; k <= ax.P; ++k) ax.chunk_b[k] = (int)((long long)k * n / ax.P);
 }
 
 bool set_window(AxisSetup& ax, int wk) {

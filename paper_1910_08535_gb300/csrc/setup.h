@@ -53,6 +53,10 @@ std::string build_axis(AxisSetup& ax, int n_elem, int p, int nq, int test, int b
 // 0 or 1 from row to row or a row's columns do not fit its window.
 bool set_window(AxisSetup& ax, int wk);
 
+// Chooses the chunking of the partitioned line solve for an axis whose batch
+// holds `lines` independent lines (P chunks, bounds chunk_b).
+void set_chunks(AxisSetup& ax, long long lines);
+
 // Gauss-Legendre nodes/weights on [-1,1] by Newton iteration on P_nq.
 void gauss_legendre(int nq, std::vector<double>& x, std::vector<double>& w);
 

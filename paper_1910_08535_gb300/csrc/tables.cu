@@ -114,9 +114,13 @@ __global__ void fold_kernel(FoldArgs f) {
         f.A[tid] = sa;
         f.C[tid] = sc;
         f.S[tid] = ss;
-        split_double(sa, f.Ahi[tid], f.Alo[tid]);
-        split_double(sc, f.Chi[tid], f.Clo[tid]);
-        split_double(ss, f.Shi[tid], f.Slo[tid]);
+        float h, l;
+        split_double(sa, h, l);
+        f.Adf[tid] = make_float2(h, l);
+        split_double(sc, h, l);
+        f.Cdf[tid] = make_float2(h, l);
+        split_double(ss, h, l);
+        f.Sdf[tid] = make_float2(h, l);
     } else if (tid < nA + nT) {
         const int k = tid - nA;
         const int i = k / f.WQ, w = k % f.WQ;
@@ -130,7 +134,9 @@ __global__ void fold_kernel(FoldArgs f) {
             }
         }
         f.TW[k] = tw;
-        split_double(tw, f.TWhi[k], f.TWlo[k]);
+        float h, l;
+        split_double(tw, h, l);
+        f.TWdf[k] = make_float2(h, l);
     }
 }
 
