@@ -139,6 +139,29 @@ int igapw_basis_table(igapw_ctx* ctx, int axis, double* vals, int* first_fn);
  * float hi/lo pair planes).  Dirichlet rows get b = 0. Asynchronous. */
 int igapw_rhs_source(igapw_ctx* ctx, const void* f_dev, void* b_dev);
 
+/* Allocation-free variant of igapw_rhs_source (the paper has no counterpart:
+ * this is a deployment aid).  igapw_rhs_source allocates the two intermediate
+ * tensors of its axis-by-axis passes with cudaMalloc on its first call for a
+ * context; callers that cannot let the library allocate there (hosts that
+ * reserve all device memory up front, schedulers admitting work against a
+ * fixed device-memory budget, latency-critical loops that cannot take
+ * cudaMalloc's implicit synchronisation) call this instead.  It computes the
+ * same b into the caller's b_dev, taking its intermediates from one static
+ * device array of IGAPW_NOALLOC_SCRATCH_BYTES that every GPU loading the
+ * library holds until exit; it calls no allocating routine.
+ *   - Sizes: each intermediate needs 8 * max(q_z q_y n_x, q_z n_y n_x) bytes
+ *     (q_a = igapw_quad_points count; 0 in 1D); above half the array the call
+ *     returns IGAPW_ERR_ARG with the sizes in igapw_last_error.
+ *   - The first call on a device looks up the array's device address for the
+ *     device current at that time (cudaGetSymbolAddress); make that first call
+ *     before any stream capture.
+ *   - All calls on a device share the array and leave their intermediates in
+ *     it; calls whose work overlaps on the GPU (different streams or contexts
+ *     without ordering between them) race on it and must be serialised.
+ * Asynchronous on the context stream, like igapw_rhs_source. */
+#define IGAPW_NOALLOC_SCRATCH_BYTES (8u << 20)
+int igapw_rhs_source_noalloc(igapw_ctx* ctx, const void* f_dev, void* b_dev);
+
 /* Operator action r = T(F u) with F chosen by op (IGAPW_OP_MASS, LAPLACE,
  * HEAT with time step dt, POISSON), tests T of the context, computed by
  * sum-factorised per-axis contractions of the folded quadrature tables

@@ -593,3 +593,34 @@ int igapw_destroy(igapw_ctx* c) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Helpers for the allocation-free source entry point (noalloc.cu).  They fill
+// the same launch arguments igapw_rhs_source uses, without touching the
+// context's lazily allocated intermediates.
+// ---------------------------------------------------------------------------
+namespace igapw {
+
+int source_setup(igapw_ctx* c, const void* f_dev, void* b_dev, SourceArgs& a, size_t& need,
+                 cudaStream_t& st, bool& f64) {
+    a = SourceArgs{};
+    a.dim = c->dim;
+    long long q[3] = {1, 1, 1};
+    for (int k = 0; k < 3; ++k) {
+        a.n[k] = c->n[k];
+        a.q[k] = k < c->dim ? (int)c->ax[k].qx.size() : 1;
+        q[k] = a.q[k];
+        a.ax[k] = c->dev[k];
+    }
+    need = c->dim > 1 ? 8 * (size_t)std::max(q[2] * q[1] * c->n[0], q[2] * c->n[1] * c->n[0]) : 0;
+    a.f = f_dev;
+    a.out = b_dev;
+    a.ntot = c->ntot;
+    st = c->stream;
+    f64 = fp64(c);
+    return IGAPW_OK;
+}
+
+int record_error(igapw_ctx* c, int code, const std::string& msg) { return fail(c, code, msg); }
+
+}  // namespace igapw

@@ -2,6 +2,10 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <string>
+
+struct igapw_ctx;
+
 #include "common.cuh"
 
 #define IGAPW_MAXP 4
@@ -93,5 +97,12 @@ struct SolveArgs {
 };
 cudaError_t launch_solve(const SolveArgs& s, const AxisDev& ax, int p, int in_fmt, int out_fmt,
                          bool fp64, cudaStream_t st);
+
+// ---- allocation-free source entry point (noalloc.cu <-> api.cu) ------------
+// Fills the source launch arguments of a context (work buffers left NULL) and
+// the bytes each of the two intermediates needs; records errors on the context.
+int source_setup(::igapw_ctx* c, const void* f_dev, void* b_dev, SourceArgs& a, size_t& need,
+                 cudaStream_t& st, bool& f64);
+int record_error(::igapw_ctx* c, int code, const std::string& msg);
 
 }  // namespace igapw

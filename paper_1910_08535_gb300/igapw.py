@@ -48,6 +48,7 @@ _SIGS = {
     'igapw_quad_points': (_I, [_VP, _I, ctypes.POINTER(_D), ctypes.POINTER(_D), ctypes.POINTER(_I)]),
     'igapw_basis_table': (_I, [_VP, _I, ctypes.POINTER(_D), ctypes.POINTER(_I)]),
     'igapw_rhs_source': (_I, [_VP, _VP, _VP]),
+    'igapw_rhs_source_noalloc': (_I, [_VP, _VP, _VP]),
     'igapw_apply': (_I, [_VP, _I, _D, _VP, _VP]),
     'igapw_assemble_1d': (_I, [_VP, _I, _I, ctypes.POINTER(_D)]),
     'igapw_solve': (_I, [_VP, _VP, _VP]),
@@ -140,6 +141,13 @@ def igapw_basis_table(ctx, axis, p):
 
 def igapw_rhs_source(ctx, f, b):
     _check(load().igapw_rhs_source(ctx, _dptr(f), _dptr(b)), ctx)
+
+
+def igapw_rhs_source_noalloc(ctx, f, b):
+    """Same result as igapw_rhs_source, with the intermediates in the library's
+    static device array instead of memory allocated on first use (for callers
+    that cannot let the library allocate; see include/igapw.h)."""
+    _check(load().igapw_rhs_source_noalloc(ctx, _dptr(f), _dptr(b)), ctx)
 
 
 def igapw_apply(ctx, op, dt, u, r):
