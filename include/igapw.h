@@ -73,8 +73,13 @@ extern "C" {
 #define IGAPW_OP_HEAT       2  /* F u = u + dt Lap u (explicit step, Sec. 4.2)      */
 #define IGAPW_OP_POISSON    3  /* F u = -Lap u    (1D Poisson system, Sec. 4.3)     */
 
-#define IGAPW_FLAG_FP64_RESIDUAL 1  /* FP32_REFINE: form the refinement residual in FP64
-                                       instead of double-float (FP32 pairs)           */
+#define IGAPW_FLAG_FP64_RESIDUAL 1  /* FP32_REFINE: form the refinement residual of
+                                       igapw_solve (and of RHS-then-solve steps) in
+                                       FP64 instead of double-float (FP32 pairs)      */
+#define IGAPW_FLAG_STEP_RHS_SOLVE 2 /* igapw_step runs the literal sequence of Sec. 4.2:
+                                       tested RHS T(u + dt Lap u), then the Kronecker
+                                       mass solve; default is the split form (see
+                                       igapw_step)                                    */
 
 #define IGAPW_MAX_DIM    3
 #define IGAPW_MAX_DEGREE 4
@@ -184,10 +189,17 @@ int igapw_assemble_1d(igapw_ctx* ctx, int axis, int which, double* dense_host);
  * allowed. Asynchronous. */
 int igapw_solve(igapw_ctx* ctx, const void* r_dev, void* u_dev);
 
-/* nsteps explicit Euler steps of u_t = Lap u in place on u_dev: each step is
- * the tested RHS T(u + dt Lap u) followed by the mass solve [Sec. 4.2, Eq. (6)].
- * The step sequence is captured once per (dt, nsteps, u_dev) into a CUDA
- * graph and replayed. Asynchronous. */
+/* nsteps explicit Euler steps of u_t = Lap u in place on u_dev [Sec. 4.2,
+ * Eq. (6)]: every step solves M u' = T(u + dt Lap u) with the tested mass
+ * M = A_z (x) A_y (x) A_x and the tested Laplacian, A = int T_i B_j and
+ * C = int T_i B_j'' per axis.  Default (split form): the other axes' mass
+ * factors cancel against the solve, so each step runs one kernel per axis that
+ * forms g = C u along every line of that axis, solves A w = g along the same
+ * line and accumulates u' = u + dt (w_x + w_y + w_z) -- the same discrete
+ * scheme with a different rounding order.  With IGAPW_FLAG_STEP_RHS_SOLVE the
+ * step forms the RHS with igapw_apply(HEAT) and solves with igapw_solve.
+ * Needs a mass-matrix context (op != POISSON).  The step sequence is captured
+ * once per (dt, nsteps, u_dev) into a CUDA graph and replayed. Asynchronous. */
 int igapw_step(igapw_ctx* ctx, double dt, int nsteps, void* u_dev);
 
 /* Same as igapw_step with HOST buffers: copies u_host (pinned memory gives an

@@ -255,6 +255,28 @@ int enqueue_apply(igapw_ctx* c, int mode, double alpha, double beta, const void*
 }
 
 int enqueue_steps(igapw_ctx* c, double dt, int nsteps, void* u, cudaStream_t st) {
+    if (!(c->d.flags & IGAPW_FLAG_STEP_RHS_SOLVE)) {
+        // split form: one kernel per axis and step (step.cu)
+        for (int s = 0; s < nsteps; ++s) {
+            for (int ax = 0; ax < c->dim; ++ax) {
+                AxisStepArgs a{};
+                a.axis = ax;
+                for (int k = 0; k < 3; ++k) a.n[k] = c->n[k];
+                a.W = c->W;
+                a.ntot = c->ntot;
+                a.ax = c->dev[ax];
+                a.u = u;
+                a.u_out = u;
+                a.acc = c->r;
+                a.dt = dt;
+                a.status = c->status;
+                const int mode = c->dim == 1 ? 3 : (ax == 0 ? 0 : (ax == c->dim - 1 ? 2 : 1));
+                cudaError_t e = launch_axis_step(a, mode, fp64(c), c->p, st);
+                if (e != cudaSuccess) return fail(c, IGAPW_ERR_CUDA, std::string("axis step: ") + cudaGetErrorString(e));
+            }
+        }
+        return IGAPW_OK;
+    }
     for (int s = 0; s < nsteps; ++s) {
         int rc = enqueue_apply(c, MODE_OP, 1.0, dt, u, c->r, st);
         if (rc) return rc;
@@ -511,6 +533,7 @@ int igapw_solve(igapw_ctx* c, const void* r_dev, void* u_dev) {
 int igapw_step(igapw_ctx* c, double dt, int nsteps, void* u_dev) {
     if (!c) return fail(nullptr, IGAPW_ERR_ARG, "ctx is NULL");
     if (!u_dev || nsteps < 0) return fail(c, IGAPW_ERR_ARG, "bad arguments");
+    if (c->d.op == IGAPW_OP_POISSON) return fail(c, IGAPW_ERR_ARG, "explicit steps need a mass-matrix context (op != POISSON)");
     if (nsteps == 0) return IGAPW_OK;
     // graphs of up to CHUNK steps, replayed
     const int CHUNK = 50;

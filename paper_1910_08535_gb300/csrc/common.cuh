@@ -125,3 +125,22 @@ struct AxisDev {
 enum : unsigned { STATUS_NONFINITE = 1u, STATUS_SINGULAR = 2u };
 
 }  // namespace igapw
+
+namespace igapw {
+
+// ---------------------------------------------------------------------------
+// Asynchronous global -> shared copies (cp.async, 4 or 8 bytes per copy):
+// many copies stay in flight without holding registers; cp_async_wait_all()
+// followed by __syncthreads() makes them visible to the block.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+}  // namespace igapw

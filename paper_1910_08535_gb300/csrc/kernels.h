@@ -98,6 +98,25 @@ struct SolveArgs {
 cudaError_t launch_solve(const SolveArgs& s, const AxisDev& ax, int p, int in_fmt, int out_fmt,
                          bool fp64, cudaStream_t st);
 
+// ---- split explicit step (step.cu) -------------------------------------------
+// One launch per axis: for every line along `axis`, g = C u, w = A^{-1} g (with
+// one double-float refinement in pair mode), and
+//   mode 0: acc = u + dt w; 1: acc += dt w; 2: u_out = acc + dt w; 3: u_out = u + dt w.
+struct AxisStepArgs {
+    int axis;
+    int n[3];
+    int W;
+    int lines_per_block;    // x-lines staged per block (set by the launcher)
+    long long ntot;
+    AxisDev ax;
+    const void* u;
+    void* u_out;
+    void* acc;
+    double dt;
+    unsigned* status;
+};
+cudaError_t launch_axis_step(const AxisStepArgs& a, int mode, bool fp64, int p, cudaStream_t st);
+
 // ---- allocation-free source entry point (noalloc.cu <-> api.cu) ------------
 // Fills the source launch arguments of a context (work buffers left NULL) and
 // the bytes each of the two intermediates needs; records errors on the context.

@@ -4,8 +4,9 @@ by element over every coefficient, in the launch configuration bench.py times:
   heat2d  quadratic, 256^2 elements, 3x3 Gauss, dt = 0.1 h^2, 200 steps,
           initial Gaussian bump + 1e-3 noise; FP64 and FP32 pairs.
   heat3d  cubic, 128^3 elements, 4^3 Gauss, dt = 0.05 h^2, 50 steps,
-          coefficients 1e-2 N(0,1); FP32 pairs, double-float (flags 0) and FP64
-          (flags 1) refinement residual.
+          coefficients 1e-2 N(0,1); FP32 pairs.
+Step forms: flags 0 = split form (one kernel per axis), 2 = RHS then solve
+(double-float residual), 3 = RHS then solve with an FP64 residual.
 
 The quadratic PW step at dt = 0.1 h^2 lies beyond the forward-Euler limit
 (the largest PW eigenvalue magnitude of the 1D operator is about 12/h^2, so
@@ -48,15 +49,16 @@ def _run(name, test, prec, flags=0):
 
 @pytest.mark.parametrize('test', ['pw', 'galerkin'])
 @pytest.mark.parametrize('prec', ['fp64', 'fp32r'])
-def test_heat2d_full(test, prec):
-    got, ref = _run('heat2d', test, prec)
+@pytest.mark.parametrize('flags', [0, 2])
+def test_heat2d_full(test, prec, flags):
+    got, ref = _run('heat2d', test, prec, flags)
     err = rel_l2(got, ref)
-    print(f'heat2d {test} {prec}: rel-L2 {err:.3e} max-abs {np.abs(got - ref).max():.3e}')
+    print(f'heat2d {test} {prec} flags={flags}: rel-L2 {err:.3e} max-abs {np.abs(got - ref).max():.3e}')
     assert err < TOL[prec]
 
 
 @pytest.mark.parametrize('test', ['pw', 'galerkin'])
-@pytest.mark.parametrize('flags', [0, 1])
+@pytest.mark.parametrize('flags', [0, 2, 3])
 def test_heat3d_full(test, flags):
     got, ref = _run('heat3d', test, 'fp32r', flags)
     err = rel_l2(got, ref)

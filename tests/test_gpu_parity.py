@@ -59,15 +59,23 @@ def test_apply_solve_step(d, ne, p, test, prec):
     sol = c.to_numpy(c.solve(c.from_numpy(rhs)))
     ref = tensor.ads_solve(tensor.mass_mats(axes), rhs)
     assert rel_l2(sol, ref) < tol, rel_l2(sol, ref)
-    # explicit steps (stable step size)
+    # explicit steps (stable step size), split form and RHS-then-solve form
     h = 1.0 / (np.max(ne) if d > 1 else ne)
     dt = 0.05 * h * h / d
+    ref = heat.run(axes, u, dt, 3)
     c.step(ud, dt, 3)
     got = c.to_numpy(ud)
-    ref = heat.run(axes, u, dt, 3)
     assert rel_l2(got, ref) < tol, rel_l2(got, ref)
     c.sync()
     c.close()
+    from paper_1910_08535_gb300 import igapw
+    c2 = _ctx(dim=d, n_elem=ne, degree=p, nq=p + 1, test=test, precision=prec, flags=igapw.IGAPW_FLAG_STEP_RHS_SOLVE)
+    ud2 = c2.from_numpy(u)
+    c2.step(ud2, dt, 3)
+    got2 = c2.to_numpy(ud2)
+    assert rel_l2(got2, ref) < tol, rel_l2(got2, ref)
+    c2.sync()
+    c2.close()
 
 
 @pytest.mark.parametrize('d,ne', [(1, 9), (2, [6, 5]), (3, [4, 3, 5])])
