@@ -230,29 +230,39 @@ def run_native(args, rank, world):
     value_g = world * ntot * nsteps * args.steps / t_g
     cg.close()
 
-    # dominant kernel: the operator-action contraction (double-float RHS),
-    # timed alone on the context stream over the same state (L2 flushed)
-    kt = []
-    r = c.empty()
+    # dominant kernels: the three per-axis step launches (axis_step_kernel),
+    # timed as one explicit step (a one-step graph) on the context stream with
+    # L2 flushed before each; the work is double-float arithmetic on the FP32
+    # pipes, so the roofline is the FP32 issue rate (ALU-bound).
+    one = []
     with torch.cuda.stream(stream):
         for i in range(23):
+            u.copy_(init)
             flush.fill_(1.0)
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            c.apply('heat', u, dt, out=r)
+            c.step(u, dt, 1)
             e1.record(stream)
             e1.synchronize()
             if i >= 3:
-                kt.append(e0.elapsed_time(e1) / 1e3)
-    k_avg = sum(kt) / len(kt)
-    alg_bytes = 16.0 * ntot               # read the u pair, write the r pair
+                one.append(e0.elapsed_time(e1) / 1e3)
+    t_one = sum(one) / len(one)
     pk = peaks()
+    W = 5                                   # PW cubic window (Galerkin: 7)
+    ops_per_dof_axis = 23 * W + 32          # see the design doc: double-float g = C u, residual, 2 FP32 solves, update
+    alg_ops = ntot * 3 * ops_per_dof_axis   # one step = 3 axis launches
+    sm_mhz = pk.get('sm_max_mhz', 2070.0)
+    alu_peak = 152 * 128 * sm_mhz * 1e6 / 1e12
+    achieved = alg_ops / t_one / 1e12
+    roof = {'bound': 'alu', 'achieved': achieved, 'peak': alu_peak, 'unit': 'TFLOP/s', 'frac': achieved / alu_peak,
+            'traffic': None, 'kernel': 'axis_step_kernel<DF,3,5,*> x3 (one explicit step, PW)',
+            'peak_kind': f'derived: 152 SMs x 128 FP32 lanes x {sm_mhz:.0f} MHz (FP32 operations/s, FMA = 1)',
+            'alg_ops_per_step': alg_ops, 'step_us': t_one * 1e6}
     hbm_peak = pk.get('hbm_gbs', 6800.0)
-    achieved = alg_bytes / k_avg / 1e9
-    roof = {'bound': 'hbm', 'achieved': achieved, 'peak': hbm_peak, 'unit': 'GB/s', 'frac': achieved / hbm_peak,
-            'traffic': None, 'kernel': 'contract_kernel<3,5,32,8,DF,MODE_OP,PAIR> (PW operator action)',
-            'peak_kind': 'measured (MEASURED_PEAKS.json hbm_gbs)' if 'hbm_gbs' in pk else 'fallback'}
+    hbm_view = {'alg_bytes_per_dof_step': 16, 'achieved_gbs': 16.0 * ntot / t_one / 1e9, 'peak_gbs': hbm_peak,
+                'frac': 16.0 * ntot / t_one / 1e9 / hbm_peak,
+                'note': 'state is L2-resident across the 50 steps of a run; the step is ALU-bound (double-float)'}
 
     # end to end through the public C ABI with host buffers (pinned)
     host = torch.empty((2,) + c.shape, dtype=torch.float32).pin_memory()
@@ -274,7 +284,7 @@ def run_native(args, rank, world):
     if rank == 0 and world == 1:
         cpu = cpu_baseline_oracle(steps=20)
         cpu.pop('seconds', None)
-    launches_per_time_step = 8
+    launches_per_time_step = 3
     line = {'metric': METRIC, 'value': value, 'unit': 'DOF-updates/s', 'n_gpus': world, 'steps': args.steps,
             'warmup': args.warmup, 'ms_per_step': t_pw / args.steps * 1e3, 'higher_is_better': True,
             'scaling': 'weak', 'vs_baseline': None, 'dtype': 'f32 pairs (double-float) + fp64 residual'
@@ -284,7 +294,7 @@ def run_native(args, rank, world):
                                    '4x4x4 Gauss, dt=0.05h^2, 50 steps per bench step, PW tests',
                        'l2': 'flushed (512 MB write) before every timed step', 'residual': args.residual},
             'galerkin': {'value': value_g, 'unit': 'DOF-updates/s', 'pw_over_galerkin': value / value_g},
-            'roofline': roof, 'clocks': clocks, 'e2e': e2e,
+            'roofline': roof, 'hbm_view': hbm_view, 'clocks': clocks, 'e2e': e2e,
             'gpu_launches': launches_per_time_step * nsteps * args.steps,
             'cpu_baseline': cpu}
     if rank == 0:

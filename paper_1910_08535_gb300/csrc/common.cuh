@@ -51,6 +51,16 @@ struct DFAcc {
         s = s2;
         c += err + e;
     }
+    // s + c += t * v with v a plain float (its low part is zero)
+    __device__ __forceinline__ void add_prod_f(DF t, float v) {
+        float p = t.hi * v;
+        float e = fmaf(t.hi, v, -p);
+        e = fmaf(t.lo, v, e);
+        float s2, err;
+        two_sum(s, p, s2, err);
+        s = s2;
+        c += err + e;
+    }
     // s + c += v
     __device__ __forceinline__ void add(DF v) {
         float s2, err;

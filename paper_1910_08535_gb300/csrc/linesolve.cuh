@@ -392,13 +392,73 @@ __device__ __forceinline__ void group_solve_reg(T* x, const int st, const int ls
     }
 }
 
-// Dispatch between the register-resident and the shared-memory solve.
+// Sequential solve of one whole line by one lane (P = 1), for batches with
+// many lines.  Values stream through a register prefetch ring of D rows so no
+// shared-memory load sits on the recurrence; the farthest band entries are
+// applied first so each row waits on its predecessor for one FMA.
+template <typename T, int KP, int D>
+__device__ __forceinline__ void seq_solve(T* x, const int st, const int n, const SolveSmem<T>& S) {
+    T w[KP];
+#pragma unroll
+    for (int m = 0; m < KP; ++m) w[m] = T(0);
+    T pf[D];
+#pragma unroll
+    for (int k = 0; k < D; ++k) pf[k] = k < n ? x[k * st] : T(0);
+    for (int i0 = 0; i0 < n; i0 += D) {
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+            const int i = i0 + k;
+            if (i < n) {
+                const T xi = pf[k];
+                pf[k] = (i + D < n) ? x[(i + D) * st] : T(0);
+                T acc = xi;
+#pragma unroll
+                for (int m = KP - 1; m >= 0; --m) acc -= S.L[i * KP + m] * w[m];
+                x[i * st] = acc;
+#pragma unroll
+                for (int m = KP - 1; m > 0; --m) w[m] = w[m - 1];
+                w[0] = acc;
+            }
+        }
+    }
+#pragma unroll
+    for (int m = 0; m < KP; ++m) w[m] = T(0);
+#pragma unroll
+    for (int k = 0; k < D; ++k) pf[k] = (n - 1 - k >= 0) ? x[(n - 1 - k) * st] : T(0);
+    for (int i0 = n - 1; i0 >= 0; i0 -= D) {
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+            const int i = i0 - k;
+            if (i >= 0) {
+                const T xi = pf[k];
+                pf[k] = (i - D >= 0) ? x[(i - D) * st] : T(0);
+                T acc = xi;
+#pragma unroll
+                for (int m = KP - 1; m >= 0; --m) acc -= S.U[i * KP + m] * w[m];
+                acc *= S.dinv[i];
+                x[i * st] = acc;
+#pragma unroll
+                for (int m = KP - 1; m > 0; --m) w[m] = w[m - 1];
+                w[0] = acc;
+            }
+        }
+    }
+}
+
+// Dispatch: sequential (P = 1), register-resident chunks, or shared-memory chunks.
 template <typename T, int KP, int NB>
 __device__ __forceinline__ void line_solve(T* x, const int st, const int lst, const int nb,
                                            const SolveSmem<T>& S, const int P, const int* bnd,
                                            const int k, const int n) {
-    if ((n + P - 1) / P <= 20) group_solve_reg<T, KP, NB, 20>(x, st, lst, nb, S, P, bnd, k);
-    else group_solve<T, KP, NB>(x, st, lst, nb, S, P, bnd, k);
+    if (P == 1) {
+#pragma unroll
+        for (int b = 0; b < NB; ++b)
+            if (b < nb) seq_solve<T, KP, 4>(x + b * lst, st, n, S);
+    } else if ((n + P - 1) / P <= 20) {
+        group_solve_reg<T, KP, NB, 20>(x, st, lst, nb, S, P, bnd, k);
+    } else {
+        group_solve<T, KP, NB>(x, st, lst, nb, S, P, bnd, k);
+    }
 }
 
 }  // namespace igapw

@@ -86,10 +86,12 @@ __global__ void __launch_bounds__(256) axis_step_kernel(const AxisStepArgs a) {
     p += align16((size_t)2 * n * W * sizeof(VT));
     int* fs = reinterpret_cast<int*>(p);
     p += align16((size_t)n * sizeof(int));
-    const int pitch = XL ? (n | 1) : NL + 1;
+    // lines carry W zero rows past n, so the contraction windows need no guards
+    const int nr = n + W;
+    const int pitch = XL ? (nr | 1) : NL + 1;
     const int st = XL ? 1 : pitch;      // row stride within a line
     const int lst = XL ? pitch : 1;     // line stride
-    const int cap = XL ? NL * pitch : n * pitch;
+    const int cap = XL ? NL * pitch : nr * pitch;
     VT* G = reinterpret_cast<VT*>(p);               // g (and, FP64, the solve buffer)
     VT* Ub = G + cap;                               // u during the contraction
     TS* X = reinterpret_cast<TS*>(Ub);              // FP32 pair mode: w0 ...
@@ -159,52 +161,48 @@ __global__ void __launch_bounds__(256) axis_step_kernel(const AxisStepArgs a) {
         }
     };
 
+    // visits every staged (line, row) of the block, rows [r0, r1), without divisions
+    auto for_each = [&](int r0, int r1, auto&& f) {
+        if (XL) {
+            for (int l = warp; l < nl; l += nw)
+                for (int i = r0 + lane; i < r1; i += 32) f(l, i);
+        } else {
+            for (int i = r0 + warp; i < r1; i += nw) f(lane, i);
+        }
+    };
+
     // ---- P0: stage u ---------------------------------------------------------
     stage(Ub, a.u);
+    for_each(n, nr, [&](int l, int i) { Ub[i * st + l * lst] = VT{}; });
     cp_async_wait_all();
     __syncthreads();
 
     // ---- P1: g = C u along the line (compensated in pair mode) --------------
-    const int total = (XL ? nl : NL) * n;
-    for (int e = threadIdx.x; e < total; e += blockDim.x) {
-        int l, i;
-        if (XL) { l = e / n; i = e - l * n; }
-        else { i = e >> 5; l = e & 31; }
-        const int j0 = fs[i];
+    for_each(0, n, [&](int l, int i) {
+        const VT* ub = Ub + fs[i] * st + l * lst;
+        const VT* ct = Ct + i * W;
         if constexpr (DFM) {
             DFAcc acc;
             acc.init();
 #pragma unroll
-            for (int w = 0; w < W; ++w) {
-                const int j = j0 + w;
-                if (j < n) acc.add_prod(Ct[i * W + w], Ub[j * st + l * lst]);
-            }
-            const DF g = acc.result();
-            G[i * st + l * lst] = g;
+            for (int w = 0; w < W; ++w) acc.add_prod(ct[w], ub[w * st]);
+            G[i * st + l * lst] = acc.result();
         } else {
             double s = 0.0;
 #pragma unroll
-            for (int w = 0; w < W; ++w) {
-                const int j = j0 + w;
-                if (j < n) s = fma(Ct[i * W + w], Ub[j * st + l * lst], s);
-            }
+            for (int w = 0; w < W; ++w) s = fma(ct[w], ub[w * st], s);
             G[i * st + l * lst] = s;
         }
-    }
+    });
     __syncthreads();
 
     const int P = LS.P;
     const int groups = 32 / P;
     const int grp = lane / P, k = lane - grp * P;
-    const int nlines_b = XL ? nl : NL;
+    const int nlines_b = XL ? nl : NL;   // lines per group set: groups = 32 / P
     if constexpr (DFM) {
         // ---- P2: w0 = A^{-1} g_hi (FP32) ------------------------------------
-        for (int e = threadIdx.x; e < total; e += blockDim.x) {
-            int l, i;
-            if (XL) { l = e / n; i = e - l * n; }
-            else { i = e >> 5; l = e & 31; }
-            X[i * st + l * lst] = G[i * st + l * lst].hi;
-        }
+        for_each(0, nr, [&](int l, int i) { X[i * st + l * lst] = i < n ? G[i * st + l * lst].hi : 0.f; });
         __syncthreads();
         for (int base = warp * groups; base < nlines_b; base += nw * groups) {
             const int first = base + grp;
@@ -213,25 +211,17 @@ __global__ void __launch_bounds__(256) axis_step_kernel(const AxisStepArgs a) {
         }
         __syncthreads();
         // ---- P3: rho = g - A w0 (double-float) ------------------------------
-        for (int e = threadIdx.x; e < total; e += blockDim.x) {
-            int l, i;
-            if (XL) { l = e / n; i = e - l * n; }
-            else { i = e >> 5; l = e & 31; }
-            const int j0 = fs[i];
+        for_each(0, n, [&](int l, int i) {
+            const TS* xw = X + fs[i] * st + l * lst;
+            const VT* at = At + i * W;
             DFAcc acc;
             const DF g = G[i * st + l * lst];
             acc.s = g.hi;
             acc.c = g.lo;
 #pragma unroll
-            for (int w = 0; w < W; ++w) {
-                const int j = j0 + w;
-                if (j < n) {
-                    const DF t = At[i * W + w];
-                    acc.add_prod(DF{-t.hi, -t.lo}, DF{X[j * st + l * lst], 0.f});
-                }
-            }
+            for (int w = 0; w < W; ++w) acc.add_prod_f(DF{-at[w].hi, -at[w].lo}, xw[w * st]);
             R[i * st + l * lst] = acc.result().hi;
-        }
+        });
         __syncthreads();
         // g is dead: prefetch the tensor the update adds to into G meanwhile
         stage(G, (MODE == 0 || MODE == 3) ? a.u : a.acc);
@@ -313,7 +303,7 @@ static cudaError_t run_axis_step(const AxisStepArgs& a0, cudaStream_t st) {
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&lim, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     auto smem_for = [&](int nl) {
-        const int cap = xl ? nl * (n | 1) : n * (32 + 1);
+        const int cap = xl ? nl * ((n + W) | 1) : (n + W) * (32 + 1);
         return align16(table_elems<TS, KP>(n) * sizeof(TS)) + align16((size_t)2 * n * W * sizeof(VT)) +
                align16((size_t)n * sizeof(int)) + (size_t)2 * cap * sizeof(VT);
     };
