@@ -175,6 +175,100 @@ def run_reference(args, rank, world):
     print(json.dumps(line))
 
 
+def _time_events(stream, fn, reps, flush=None, warm=3):
+    """Average device time of fn() over reps calls (CUDA events on `stream`,
+    L2 flushed before each call when a flush buffer is given)."""
+    import torch
+    out = []
+    with torch.cuda.stream(stream):
+        for i in range(warm + reps):
+            if flush is not None:
+                flush.fill_(1.0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            if i >= warm:
+                out.append(e0.elapsed_time(e1) / 1e3)
+    return sum(out) / len(out)
+
+
+def measure_rows(ctx_pw, u, dt, stream, flush, hbm_peak):
+    """Rows a3 (operator action) and a6 (refined Kronecker solve) on heat3d:
+    device time per call, bytes per DOF moved by the algorithm, and the
+    oracle's CPU time for the same operation."""
+    import numpy as np
+    from oracle import systems, tensor
+    from paper_1910_08535_gb300 import workloads
+    n = ctx_pw.ntot
+    r = ctx_pw.empty()
+    out = ctx_pw.empty()
+    t_apply = _time_events(stream, lambda: ctx_pw.apply('heat', u, dt, out=r), 10, flush)
+    t_solve = _time_events(stream, lambda: ctx_pw.solve(r, out=out), 10, flush)
+    w = workloads.WORKLOADS[WORKLOAD]
+    axes = [systems.Axis(w['n_elem'], w['degree'], w['nq'], 'pw') for _ in range(3)]
+    M, L = tensor.mass_mats(axes), tensor.lap_mats(axes)
+    u0 = workloads.initial_state(WORKLOAD)
+    t0 = time.perf_counter()
+    rr = tensor.apply_heat_system(axes, u0, dt, M, L)
+    t1 = time.perf_counter()
+    tensor.ads_solve(M, rr)
+    t2 = time.perf_counter()
+    return {
+        'a3_apply_heat': {'us': t_apply * 1e6, 'dof_per_s': n / t_apply,
+                          'hbm_frac_16B_per_dof': 16.0 * n / t_apply / 1e9 / hbm_peak,
+                          'kernel': 'contract_kernel (7 double-float banded passes)',
+                          'oracle_cpu_s': t1 - t0},
+        'a6_solve_refined': {'us': t_solve * 1e6, 'dof_per_s': n / t_solve,
+                             'kernels': '3 FP32 line solves + double-float residual + 3 line solves',
+                             'oracle_cpu_s': t2 - t1},
+    }
+
+
+def measure_source_table1(stream, flush, hbm_peak, reps=5):
+    """Row a4 on the paper's Table 1 experiment (Sec. 4.1): 3D L2-projection
+    RHS for a tensor-product cubic polynomial, quadratic C1 splines, 128^3
+    elements; B-spline tests with 3 Gauss points per element, PW tests with 2
+    (the cubic integrand on each cell needs only 2).  f is sampled at each
+    rule's points (FP32), the RHS accumulates in double-float."""
+    import numpy as np
+    import torch
+    from oracle import systems, tensor
+    from paper_1910_08535_gb300 import workloads
+    from paper_1910_08535_gb300.igapw import Context
+    ne, p = 128, 2
+    cub = [lambda x: 2 * x ** 3 - x ** 2 + 0.5 * x + 1, lambda x: x ** 3 + 0.3 * x + 0.2,
+           lambda x: -x ** 3 + 2 * x ** 2 + 1]
+    res = {}
+    for test, nq in (('pw', 2), ('galerkin', 3)):
+        with torch.cuda.stream(stream):
+            c = Context(dim=3, n_elem=ne, degree=p, nq=nq, test=test, precision='fp32r', op='mass', stream=stream)
+            pts = [c.quad_points(a)[0] for a in range(3)]
+            f = torch.from_numpy(workloads.tensor_samples(pts, [tuple(cub)]).astype(np.float32)).cuda()
+            b = c.empty()
+            t = _time_events(stream, lambda: c.rhs_source(f, out=b), reps, flush)
+            c.sync()
+        q = [len(x) for x in pts]
+        fbytes = 4 * q[0] * q[1] * q[2]
+        alg = fbytes + 8 * c.ntot
+        axes = [systems.Axis(ne, p, nq, test) for _ in range(3)]
+        fh = f.cpu().numpy().astype(np.float64)
+        t0 = time.perf_counter()
+        ref = tensor.rhs_source(axes, fh)
+        tcpu = time.perf_counter() - t0
+        got = c.to_numpy(b)
+        err = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+        res[test] = {'nq': nq, 'points': q[0] * q[1] * q[2], 'us': t * 1e6, 'dof_per_s': c.ntot / t,
+                     'alg_bytes': alg, 'achieved_gbs': alg / t / 1e9, 'hbm_frac': alg / t / 1e9 / hbm_peak,
+                     'rel_l2_vs_oracle': err, 'oracle_cpu_s': tcpu}
+        c.close()
+        del f, b
+    res['pw_speedup_over_galerkin'] = res['galerkin']['us'] / res['pw']['us']
+    return res
+
+
 def run_native(args, rank, world):
     import numpy as np
     import torch
@@ -280,6 +374,9 @@ def run_native(args, rank, world):
     e2e = {'value': world * ntot * nsteps * args.steps / e2e_total, 'unit': 'DOF-updates/s',
            'h2d_bytes_per_step': 8 * ntot, 'd2h_bytes_per_step': 8 * ntot}
 
+    rows = measure_rows(c, u, dt, stream, flush, hbm_peak)
+    rows['a4_source_table1'] = measure_source_table1(stream, flush, hbm_peak)
+
     cpu = None
     if rank == 0 and world == 1:
         cpu = cpu_baseline_oracle(steps=20)
@@ -294,7 +391,7 @@ def run_native(args, rank, world):
                                    '4x4x4 Gauss, dt=0.05h^2, 50 steps per bench step, PW tests',
                        'l2': 'flushed (512 MB write) before every timed step', 'residual': args.residual},
             'galerkin': {'value': value_g, 'unit': 'DOF-updates/s', 'pw_over_galerkin': value / value_g},
-            'roofline': roof, 'hbm_view': hbm_view, 'clocks': clocks, 'e2e': e2e,
+            'roofline': roof, 'hbm_view': hbm_view, 'clocks': clocks, 'e2e': e2e, 'rows': rows,
             'gpu_launches': launches_per_time_step * nsteps * args.steps,
             'cpu_baseline': cpu}
     if rank == 0:

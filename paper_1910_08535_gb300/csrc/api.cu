@@ -467,9 +467,10 @@ int igapw_rhs_source(igapw_ctx* c, const void* f_dev, void* b_dev) {
         q[k] = a.q[k];
         a.ax[k] = c->dev[k];
     }
-    // intermediates: after the x pass (q_z q_y n_x), after the y pass (q_z n_y n_x)
+    a.pw = c->d.test == IGAPW_PWCONST;
+    // Galerkin intermediates: after the x pass (q_z q_y n_x), after the y pass (q_z n_y n_x)
     const size_t need = 8 * (size_t)std::max(q[2] * q[1] * c->n[0], q[2] * c->n[1] * c->n[0]);
-    if (c->dim > 1 && c->src_bytes < need) {
+    if (!a.pw && c->dim > 1 && c->src_bytes < need) {
         CKC(c, cudaStreamSynchronize(c->stream));
         unsigned char *b0 = nullptr, *b1 = nullptr;
         CKC(c, dalloc(c, &b0, need));
@@ -635,7 +636,8 @@ int source_setup(igapw_ctx* c, const void* f_dev, void* b_dev, SourceArgs& a, si
         q[k] = a.q[k];
         a.ax[k] = c->dev[k];
     }
-    need = c->dim > 1 ? 8 * (size_t)std::max(q[2] * q[1] * c->n[0], q[2] * c->n[1] * c->n[0]) : 0;
+    a.pw = c->d.test == IGAPW_PWCONST;
+    need = (c->dim > 1 && !a.pw) ? 8 * (size_t)std::max(q[2] * q[1] * c->n[0], q[2] * c->n[1] * c->n[0]) : 0;
     a.f = f_dev;
     a.out = b_dev;
     a.ntot = c->ntot;

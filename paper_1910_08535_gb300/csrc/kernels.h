@@ -68,9 +68,11 @@ struct ContractArgs {
 cudaError_t launch_contract(const ContractArgs& a, int mode, int cmp, int io, cudaStream_t st);
 
 // ---- source right-hand side (rhs.cu) ----------------------------------------
-// b = (TW_z (x) TW_y (x) TW_x) f over the quadrature grid, one axis per pass.
+// b = (TW_z (x) TW_y (x) TW_x) f over the quadrature grid: PW tests in one
+// fused pass (every point belongs to one cell), Galerkin one axis per pass.
 struct SourceArgs {
     int dim;
+    int pw;                 // PW tests: one fused pass, no intermediates
     int n[3];               // coefficients per axis
     int q[3];               // points per axis
     AxisDev ax[3];

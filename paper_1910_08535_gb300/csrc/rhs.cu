@@ -489,8 +489,74 @@ __global__ void __launch_bounds__(256) source_pass_kernel(const void* in, void* 
     (void)nout_total;
 }
 
+// ---------------------------------------------------------------------------
+// Kernel (b-src), PW tests: every quadrature point lies in exactly one test
+// cell per axis, so b[k][j][i] is the weighted sum of the samples of the cell
+// (k, j, i) alone (Sec. 4.1 PW loop: weight times 1.0) -- one thread per
+// coefficient, each sample read once, x-neighbouring threads reading
+// neighbouring cells (coalesced).  Pair mode: x sums in double-float, the
+// y/z weight products exact (df_mul), accumulation compensated.
+// ---------------------------------------------------------------------------
+template <typename CT, int IN_F32>
+__global__ void __launch_bounds__(256) source_pw_kernel(const SourceArgs a) {
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int nx = a.n[0], ny = a.n[1], nz = a.n[2];
+    if (e >= (long long)nx * ny * nz) return;
+    const int i = (int)(e % nx);
+    const long long t = e / nx;
+    const int j = (int)(t % ny);
+    const int k = (int)(t / ny);
+    const int Qx = a.q[0], Qy = a.q[1], Qz = a.q[2];
+    const AxisDev& X = a.ax[0];
+    const int wx = X.wq, psx = X.pstart[i];
+    const int wy = a.dim >= 2 ? a.ax[1].wq : 1, psy = a.dim >= 2 ? a.ax[1].pstart[j] : 0;
+    const int wz = a.dim >= 3 ? a.ax[2].wq : 1, psz = a.dim >= 3 ? a.ax[2].pstart[k] : 0;
+    Acc<CT> acc;
+    acc.init();
+    for (int az = 0; az < wz; ++az) {
+        const int qz = psz + az;
+        if (qz >= Qz) break;
+        const CT tz = a.dim >= 3 ? tab<CT>(a.ax[2].TW, k * wz + az) : from_double<CT>(1.0);
+        for (int by = 0; by < wy; ++by) {
+            const int qy = psy + by;
+            if (qy >= Qy) break;
+            const CT ty = a.dim >= 2 ? tab<CT>(a.ax[1].TW, j * wy + by) : from_double<CT>(1.0);
+            const long long row = ((long long)qz * Qy + qy) * Qx;
+            Acc<CT> sx;
+            sx.init();
+            for (int c = 0; c < wx; ++c) {
+                const int qx = psx + c;
+                if (qx >= Qx) break;
+                const CT tw = tab<CT>(X.TW, i * wx + c);
+                if constexpr (std::is_same<CT, double>::value) {
+                    const double fv = IN_F32 ? (double)((const float*)a.f)[row + qx] : ((const double*)a.f)[row + qx];
+                    sx.add_prod(tw, fv);
+                } else {
+                    sx.add_prod_f(tw, ((const float*)a.f)[row + qx]);
+                }
+            }
+            if constexpr (std::is_same<CT, double>::value) acc.add_prod(tz * ty, sx.result());
+            else acc.add_prod(df_mul(tz, ty), sx.result());
+        }
+    }
+    const CT r = acc.result();
+    if constexpr (std::is_same<CT, double>::value) {
+        ((double*)a.out)[e] = r;
+    } else {
+        ((float*)a.out)[e] = r.hi;
+        ((float*)a.out)[e + a.ntot] = r.lo;
+    }
+}
+
 cudaError_t launch_source(const SourceArgs& a, int fp64, cudaStream_t st) {
-    // passes: x (Ni = 1), then y (Ni = n_x), then z (Ni = n_x n_y)
+    if (a.pw) {
+        const long long total = (long long)a.n[0] * a.n[1] * a.n[2];
+        const unsigned blocks = (unsigned)((total + 255) / 256);
+        if (fp64) source_pw_kernel<double, 0><<<blocks, 256, 0, st>>>(a);
+        else source_pw_kernel<DF, 1><<<blocks, 256, 0, st>>>(a);
+        return cudaGetLastError();
+    }
+    // Galerkin: passes x (Ni = 1), then y (Ni = n_x), then z (Ni = n_x n_y)
     const int d = a.dim;
     long long dims_in[3] = {a.q[0], d >= 2 ? a.q[1] : 1, d >= 3 ? a.q[2] : 1};
     const void* src = a.f;
