@@ -138,7 +138,9 @@ int igapw_basis_table(igapw_ctx* ctx, int axis, double* vals, int* first_fn);
 
 /* Source right-hand side b = int T_i f over the tensor grid of quadrature
  * points: PW sums the quadrature weights times f over each cell (the test is
- * 1), Galerkin multiplies by the test B-splines [Sec. 4.1 generation loops].
+ * 1; one fused pass, every sample read once), Galerkin multiplies by the test
+ * B-splines (one pass per axis through intermediates allocated on the first
+ * call) [Sec. 4.1 generation loops].
  * f_dev: device, FP64 (FP64 mode) or float (FP32_REFINE) samples on the
  * igapw_quad_points grid.  b_dev: device coefficient-shaped tensor (double, or
  * float hi/lo pair planes).  Dirichlet rows get b = 0. Asynchronous. */
@@ -154,9 +156,10 @@ int igapw_rhs_source(igapw_ctx* ctx, const void* f_dev, void* b_dev);
  * same b into the caller's b_dev, taking its intermediates from one static
  * device array of IGAPW_NOALLOC_SCRATCH_BYTES that every GPU loading the
  * library holds until exit; it calls no allocating routine.
- *   - Sizes: each intermediate needs 8 * max(q_z q_y n_x, q_z n_y n_x) bytes
- *     (q_a = igapw_quad_points count; 0 in 1D); above half the array the call
- *     returns IGAPW_ERR_ARG with the sizes in igapw_last_error.
+ *   - Sizes: with B-spline tests each intermediate needs
+ *     8 * max(q_z q_y n_x, q_z n_y n_x) bytes (q_a = igapw_quad_points count);
+ *     PW tests (one fused pass) and 1D need none.  Above half the array the
+ *     call returns IGAPW_ERR_ARG with the sizes in igapw_last_error.
  *   - The first call on a device looks up the array's device address for the
  *     device current at that time (cudaGetSymbolAddress); make that first call
  *     before any stream capture.
