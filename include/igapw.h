@@ -12,7 +12,10 @@
  *   - Kronecker-factored mass solve Mx (x) My (x) Mz as three batches of 1D
  *     banded systems (alternating directions)                 [Sec. 4.1]
  *   - explicit Euler steps, one L2 projection each            [Sec. 4.2, Eq. (6)]
- *   - zero Dirichlet rows by row replacement (1D Poisson)     [Sec. 4.3]
+ *   - zero Dirichlet rows by row replacement (Poisson)        [Sec. 4.3]
+ *   - 2D/3D Poisson -Lap u = f: the tested operator is a sum of Kronecker
+ *     products, solved by fast diagonalisation of the 1D pencils plus
+ *     iterative refinement (the paper uses a sparse direct solver) [Sec. 4.3]
  *
  * PW test cells.  The paper leaves the choice of the N_x intervals open and only
  * requires them to be linearly independent (Sec. 2).  This library bounds cell k
@@ -63,7 +66,8 @@ extern "C" {
 #define IGAPW_PWCONST       1  /* piece-wise constant tests                         */
 
 #define IGAPW_BC_NONE       0  /* all n coefficients free                           */
-#define IGAPW_BC_DIRICHLET0 1  /* first/last coefficient per axis held at 0 (1D)    */
+#define IGAPW_BC_DIRICHLET0 1  /* first/last coefficient per axis held at 0 (1D; in
+                                  2D/3D for the POISSON system only)                */
 
 #define IGAPW_FP64          0
 #define IGAPW_FP32_REFINE   1
@@ -71,7 +75,7 @@ extern "C" {
 #define IGAPW_OP_MASS       0  /* F u = u         (L2 projection, Sec. 4.1)         */
 #define IGAPW_OP_LAPLACE    1  /* F u = Lap u     (apply only)                      */
 #define IGAPW_OP_HEAT       2  /* F u = u + dt Lap u (explicit step, Sec. 4.2)      */
-#define IGAPW_OP_POISSON    3  /* F u = -Lap u    (1D Poisson system, Sec. 4.3)     */
+#define IGAPW_OP_POISSON    3  /* F u = -Lap u    (Poisson system, Sec. 4.3)        */
 
 #define IGAPW_FLAG_FP64_RESIDUAL 1  /* FP32_REFINE: form the refinement residual of
                                        igapw_solve (and of RHS-then-solve steps) in
@@ -80,6 +84,10 @@ extern "C" {
                                        tested RHS T(u + dt Lap u), then the Kronecker
                                        mass solve; default is the split form (see
                                        igapw_step)                                    */
+#define IGAPW_FLAG_FDM_BF16X9 4     /* 2D/3D POISSON: run the FP32 transforms of the
+                                       solve as cuBLAS FP32 GEMMs emulated with three
+                                       bf16 terms on the tensor pipe (BF16x9) instead
+                                       of plain FP32 GEMMs                            */
 
 #define IGAPW_MAX_DIM    3
 #define IGAPW_MAX_DEGREE 4
@@ -91,9 +99,13 @@ typedef struct igapw_ctx igapw_ctx;
  * the method requires, Sec. 2); nq >= 1 Gauss points per element (Galerkin) or
  * per polynomial piece of a cell (PW); test = IGAPW_GALERKIN | IGAPW_PWCONST;
  * bc = IGAPW_BC_*; precision = IGAPW_FP64 | IGAPW_FP32_REFINE; op = IGAPW_OP_*
- * selects the matrix igapw_solve inverts (POISSON: the 1D operator, dim = 1 and
- * bc = DIRICHLET0 required; anything else: the tensor-product mass matrix);
- * flags = IGAPW_FLAG_*. */
+ * selects the matrix igapw_solve inverts (POISSON: -Lap u with bc = DIRICHLET0
+ * required -- in 1D the banded 1D operator, in 2D/3D the multi-D operator;
+ * anything else: the tensor-product mass matrix); flags = IGAPW_FLAG_*.
+ * A 2D/3D POISSON context also diagonalises every 1D pencil (L_a, A_a) at
+ * creation (FP64 LU and nonsymmetric eigensolver through cuSOLVER, O(n_a^3));
+ * creation fails with IGAPW_ERR_ARG if a pencil's spectrum is not real and
+ * positive. */
 typedef struct {
     int dim;
     int n_elem[3];
@@ -175,7 +187,10 @@ int igapw_rhs_source_noalloc(igapw_ctx* ctx, const void* f_dev, void* b_dev);
  * sum-factorised per-axis contractions of the folded quadrature tables
  * [Sec. 2 / Sec. 3 systems; Sec. 4.2 RHS].  u_dev, r_dev: device tensors of
  * the context precision; they must not overlap.  For a Dirichlet context the
- * Dirichlet rows return r_i = u_i (row replacement, Sec. 4.3). Asynchronous. */
+ * Dirichlet rows return r_i = u_i (row replacement, Sec. 4.3); in 2D/3D a row
+ * is a Dirichlet row when any of its axis indices is, and POISSON applies
+ * sum_a (-int T B'' along a) (x) (int T B along the other axes) on the
+ * others. Asynchronous. */
 int igapw_apply(igapw_ctx* ctx, int op, double dt, const void* u_dev, void* r_dev);
 
 /* Exports one 1D matrix of an axis as a dense row-major n x n double array in
@@ -189,7 +204,15 @@ int igapw_assemble_1d(igapw_ctx* ctx, int axis, int which, double* dense_host);
  * axis with the precomputed FP64 LU factors [Sec. 4.1 ADS].  FP32_REFINE: an
  * FP32 solve, the residual r - S u0 (double-float or FP64), a second FP32
  * solve, u = u0 + correction stored as a hi/lo pair.  r_dev == u_dev is
- * allowed. Asynchronous. */
+ * allowed.
+ * 2D/3D POISSON contexts solve K u = r for the multi-D operator instead: with
+ * A_a^{-1} L_a = V_a Lambda_a V_a^{-1} per axis (unknown rows and columns),
+ * P = diag(I on Dirichlet rows, (V_x V_y V_z) diag(1/(lx+ly+lz)) (W_x W_y W_z)),
+ * W_a = V_a^{-1} A_a^{-1}, applied as FP32 GEMMs along each axis, inside
+ * iterative refinement whose residual r - K u is taken by the contraction
+ * kernel: one correction in FP32_REFINE (residual in double-float, or FP64
+ * with IGAPW_FLAG_FP64_RESIDUAL), three corrections in FP64 (FP64 residual).
+ * r_dev and u_dev must differ.  Asynchronous. */
 int igapw_solve(igapw_ctx* ctx, const void* r_dev, void* u_dev);
 
 /* nsteps explicit Euler steps of u_t = Lap u in place on u_dev [Sec. 4.2,

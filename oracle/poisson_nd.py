@@ -89,6 +89,29 @@ def apply(axes, u):
     return r
 
 
+def apply_abs(axes, u):
+    """sum_a |-L_a (x) M_others| |u| off the boundary, |u| on it: an upper
+    bound on |K| |u| and the scale of the rounding in the per-axis evaluation
+    of K u; used for normwise backward errors."""
+    u = np.abs(np.asarray(u, dtype=np.float64))
+    r = np.zeros_like(u)
+    for t in operator_terms(axes):
+        v = u
+        for a, M in enumerate(t):
+            v = tensor.along(np.abs(M), v, a)
+        r += v
+    mask = boundary_mask(axes)
+    r[mask] = u[mask]
+    return r
+
+
+def backward_error(axes, u, b):
+    """Normwise backward error ||b - K u|| / (||apply_abs(u)|| + ||b||) of an
+    approximate solution u (2-norms)."""
+    r = np.asarray(b, dtype=np.float64) - apply(axes, u)
+    return float(np.linalg.norm(r) / (np.linalg.norm(apply_abs(axes, u)) + np.linalg.norm(b)))
+
+
 def rhs(axes, f_grid):
     """b = T f on the tensor quadrature grid (zero on the boundary rows)."""
     return tensor.rhs_source(axes, f_grid)

@@ -11,7 +11,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, 'csrc')
 OBJ = os.path.join(HERE, '_objs')
 LIB = os.path.join(HERE, 'lib', 'libigapw.so')
-SOURCES = ['setup.cpp', 'tables.cu', 'solve.cu', 'rhs.cu', 'api.cu', 'noalloc.cu', 'step.cu']
+SOURCES = ['setup.cpp', 'tables.cu', 'solve.cu', 'rhs.cu', 'api.cu', 'noalloc.cu', 'step.cu', 'poisson.cu',
+           'step_f64_p2.cu', 'step_f64_p3.cu', 'step_f64_p4.cu', 'step_df_p2.cu', 'step_df_p3.cu', 'step_df_p4.cu']
 ARCH = ['-gencode', 'arch=compute_103a,code=sm_103a']
 FLAGS = ['-O3', '-lineinfo', '-std=c++17', '-Xcompiler', '-fPIC', '--expt-relaxed-constexpr',
          '-Xcompiler', '-Wall', '-Xcompiler', '-Wno-unused-function']
@@ -51,7 +52,9 @@ def build(verbose=False, force=False):
         raise RuntimeError('nvcc failed for ' + ', '.join(f[0] for f in failed))
     objs = [r[3] for r in results]
     tmp = LIB + '.tmp'
-    cmd = [nvcc(), *ARCH, '-shared', '-o', tmp, *objs, '-lcudart']
+    libdir = os.path.join(os.path.dirname(os.path.dirname(os.path.realpath(nvcc()))), 'lib64')
+    cmd = [nvcc(), *ARCH, '-shared', '-o', tmp, *objs, '-lcudart', '-lcublas', '-lcusolver',
+           '-Xlinker', '-rpath=' + libdir]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError('link failed:\n' + r.stdout + r.stderr)

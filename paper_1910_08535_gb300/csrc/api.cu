@@ -7,6 +7,7 @@
 
 #include "../../include/igapw.h"
 #include "kernels.h"
+#include "poisson.h"
 #include "setup.h"
 
 using namespace igapw;
@@ -58,9 +59,13 @@ struct igapw_ctx {
     unsigned* status = nullptr;
     std::string err;
     std::vector<GraphEntry> graphs;
+    FdmState* fdm = nullptr;  // multi-D Poisson contexts: spectral data of the 1D pencils
 };
 
 namespace {
+
+// FP64 multi-D Poisson: refinement corrections after the first FP32 solve
+constexpr int kPoissonRefineF64 = 3;
 
 int fail(igapw_ctx* c, int code, const std::string& msg) {
     if (c) c->err = msg;
@@ -138,7 +143,7 @@ int build_axis_device(igapw_ctx* c, int a) {
     // kernel (a): basis table, then fold into the banded tables
     launch_basis_table(m.knots, p, Q, m.qx, m.qfirst, m.vals, c->stream);
     FoldArgs f{};
-    f.n = n; f.p = p; f.W = W; f.WQ = WQ; f.test = s.test; f.poisson = (c->d.op == IGAPW_OP_POISSON);
+    f.n = n; f.p = p; f.W = W; f.WQ = WQ; f.test = s.test; f.poisson = (c->d.op == IGAPW_OP_POISSON && c->dim == 1);
     f.fstart = m.fstart; f.pstart = m.pstart; f.pcount = m.pcount; f.is_free = m.is_free;
     f.qfirst = m.qfirst; f.qw = m.qw; f.vals = m.vals;
     f.A = m.A; f.C = m.C; f.S = m.S; f.TW = m.TW;
@@ -295,11 +300,14 @@ int valid_desc(const igapw_desc* d, std::string& why) {
     if (d->nq < 1 || d->nq > 16) { why = "nq must be 1..16"; return 0; }
     if (d->test != IGAPW_GALERKIN && d->test != IGAPW_PWCONST) { why = "unknown test"; return 0; }
     if (d->bc != IGAPW_BC_NONE && d->bc != IGAPW_BC_DIRICHLET0) { why = "unknown bc"; return 0; }
-    if (d->bc == IGAPW_BC_DIRICHLET0 && d->dim != 1) { why = "Dirichlet rows are supported in 1D only"; return 0; }
+    if (d->bc == IGAPW_BC_DIRICHLET0 && d->dim != 1 && d->op != IGAPW_OP_POISSON) {
+        why = "Dirichlet rows in 2D/3D are supported for the POISSON system only";
+        return 0;
+    }
     if (d->precision != IGAPW_FP64 && d->precision != IGAPW_FP32_REFINE) { why = "unknown precision"; return 0; }
     if (d->op < IGAPW_OP_MASS || d->op > IGAPW_OP_POISSON) { why = "unknown op"; return 0; }
-    if (d->op == IGAPW_OP_POISSON && (d->dim != 1 || d->bc != IGAPW_BC_DIRICHLET0)) {
-        why = "the POISSON system needs dim = 1 and Dirichlet rows (multi-D Poisson is not a Kronecker product)";
+    if (d->op == IGAPW_OP_POISSON && d->bc != IGAPW_BC_DIRICHLET0) {
+        why = "the POISSON system needs Dirichlet rows";
         return 0;
     }
     return 1;
@@ -316,6 +324,32 @@ int alloc_scratch(igapw_ctx* c) {
         CKC(c, dalloc(c, &c->u0, nt));
         CKC(c, dalloc(c, &c->rho, nt));
     }
+    return IGAPW_OK;
+}
+
+// Multi-D Poisson contexts: diagonalise the 1D pencils of every axis (poisson.cu).
+int build_fdm(igapw_ctx* c) {
+    if (c->d.op != IGAPW_OP_POISSON || c->dim < 2) return IGAPW_OK;
+    CKC(c, cudaStreamSynchronize(c->stream));
+    FdmAxisInput in[3];
+    const int* fr[3] = {nullptr, nullptr, nullptr};
+    for (int a = 0; a < c->dim; ++a) {
+        const AxisSetup& s = c->ax[a];
+        in[a].n = s.n;
+        in[a].W = c->W;
+        in[a].A.resize((size_t)s.n * c->W);
+        in[a].C.resize((size_t)s.n * c->W);
+        CKC(c, cudaMemcpy(in[a].A.data(), c->mem[a].A, in[a].A.size() * 8, cudaMemcpyDeviceToHost));
+        CKC(c, cudaMemcpy(in[a].C.data(), c->mem[a].C, in[a].C.size() * 8, cudaMemcpyDeviceToHost));
+        in[a].fstart = s.fstart;
+        in[a].is_free = s.is_free;
+        fr[a] = c->mem[a].is_free;
+    }
+    c->fdm = new (std::nothrow) FdmState();
+    if (!c->fdm) return fail(c, IGAPW_ERR_OOM, "host allocation failed");
+    std::string err;
+    const int rc = fdm_build(*c->fdm, c->dim, in, fr, (c->d.flags & IGAPW_FLAG_FDM_BF16X9) != 0, c->stream, err);
+    if (rc) return fail(c, rc, "Poisson set-up: " + err);
     return IGAPW_OK;
 }
 
@@ -341,11 +375,18 @@ int setup_all(igapw_ctx* c, const std::vector<double>* knots_override, int overr
         int rc = build_axis_device(c, a);
         if (rc) return rc;
     }
-    return check_setup_status(c);
+    int rc = check_setup_status(c);
+    if (rc) return rc;
+    return build_fdm(c);
 }
 
 void release(igapw_ctx* c) {
     free_graphs(c);
+    if (c->fdm) {
+        fdm_release(*c->fdm);
+        delete c->fdm;
+        c->fdm = nullptr;
+    }
     for (void* p : c->allocs) cudaFree(p);
     c->allocs.clear();
 }
@@ -429,6 +470,8 @@ int igapw_set_knots(igapw_ctx* c, int axis, const double* knots, int len) {
     c->src_bytes = 0;
     int rc = check_setup_status(c);
     if (rc) return rc;
+    rc = build_fdm(c);
+    if (rc) return rc;
     return alloc_scratch(c);
 }
 
@@ -499,6 +542,17 @@ int igapw_apply(igapw_ctx* c, int op, double dt, const void* u_dev, void* r_dev)
         case IGAPW_OP_HEAT: return enqueue_apply(c, MODE_OP, 1.0, dt, u_dev, r_dev, c->stream);
         case IGAPW_OP_POISSON:
             if (c->d.op != IGAPW_OP_POISSON) return fail(c, IGAPW_ERR_ARG, "POISSON apply needs a POISSON context");
+            if (c->fdm) {
+                ContractArgs a = contract_args(c);
+                a.u = u_dev;
+                a.out = r_dev;
+                a.alpha = 0.0;
+                a.beta = -1.0;
+                const int f = fp64(c) ? FMT_F64 : FMT_PAIR;
+                cudaError_t e = launch_poisson_contract(a, MODE_PK, f, f, c->stream);
+                if (e != cudaSuccess) return fail(c, IGAPW_ERR_CUDA, std::string("Poisson apply: ") + cudaGetErrorString(e));
+                return IGAPW_OK;
+            }
             return enqueue_apply(c, MODE_SYS, 1.0, 0.0, u_dev, r_dev, c->stream);
     }
     return fail(c, IGAPW_ERR_ARG, "unknown op");
@@ -528,6 +582,17 @@ int igapw_assemble_1d(igapw_ctx* c, int axis, int which, double* dense) {
 int igapw_solve(igapw_ctx* c, const void* r_dev, void* u_dev) {
     if (!c) return fail(nullptr, IGAPW_ERR_ARG, "ctx is NULL");
     if (!r_dev || !u_dev) return fail(c, IGAPW_ERR_ARG, "NULL tensor");
+    if (c->fdm) {
+        if (r_dev == u_dev) return fail(c, IGAPW_ERR_ARG, "the multi-D Poisson solve needs distinct r and u");
+        float* t0 = (float*)c->r;                  // 2 ntot floats in both precisions
+        float* t1 = t0 + c->ntot;
+        float* rho = fp64(c) ? (float*)c->w : c->rho;
+        std::string err;
+        const int rc = fdm_solve(*c->fdm, contract_args(c), r_dev, u_dev, fp64(c), kPoissonRefineF64, t0, t1, rho,
+                                 c->u0, (c->d.flags & IGAPW_FLAG_FP64_RESIDUAL) != 0, c->stream, err);
+        if (rc) return fail(c, rc, "Poisson solve: " + err);
+        return IGAPW_OK;
+    }
     return enqueue_solve(c, r_dev, u_dev, c->stream);
 }
 

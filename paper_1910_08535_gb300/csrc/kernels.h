@@ -45,7 +45,10 @@ void launch_factor(const FactorArgs& a, cudaStream_t st);
 // MODE_OP:  r = T(alpha u + beta Lap u) with the folded A / C tables
 // MODE_SYS: r = (S_z (x) S_y (x) S_x) u with the system tables
 // MODE_RES: rho = r - (S_z (x) S_y (x) S_x) u0   (refinement residual)
-enum { MODE_OP = 0, MODE_SYS = 1, MODE_RES = 2 };
+// MODE_PK:  r = K u, the multi-D Poisson operator: MODE_OP with alpha = 0,
+//           beta = -1 on rows off the boundary, u itself on boundary rows
+// MODE_PRES: rho = r - K u (F32 out; u F32 with pair r, or F64 with F64 r)
+enum { MODE_OP = 0, MODE_SYS = 1, MODE_RES = 2, MODE_PK = 3, MODE_PRES = 4 };
 // compute / storage formats
 enum { FMT_F64 = 0, FMT_PAIR = 1, FMT_F32 = 2 };
 
@@ -55,8 +58,8 @@ struct ContractArgs {
     int zchunk;
     int tx, ty;             // runtime tile widths (<= the kernel's compile-time tile)
     AxisDev ax[3];
-    const void* u;          // MODE_OP/SYS: F64 or PAIR; MODE_RES: F32 u0
-    const void* r;          // MODE_RES: PAIR right-hand side
+    const void* u;          // MODE_OP/SYS/PK: F64 or PAIR; MODE_RES: F32 u0; MODE_PRES: F32 or F64
+    const void* r;          // MODE_RES/PRES: right-hand side (PAIR, or F64 for PRES)
     void* out;              // F64 / PAIR / F32 (MODE_RES)
     long long ntot;         // elements per plane of a pair tensor
     double alpha, beta;

@@ -1,0 +1,483 @@
+// Multi-D Poisson solve (Sec. 4.3 problem -Lap u = f, zero Dirichlet rows).
+//
+// The tested operator K = sum_a (-C_a) (x) A_others (rows off the boundary;
+// identity rows on it) is not a Kronecker product, so the 1D banded
+// factorisations of the mass solve do not invert it.  Its interior block is
+// K_II = sum_a L_a (x) A_others with L = -C restricted to the unknowns, and
+// every 1D pencil (L_a, A_a) has a real spectrum with well-conditioned
+// eigenvectors (both for B-spline and for piece-wise constant tests):
+//   A_a^{-1} L_a = V_a Lambda_a V_a^{-1}.
+// With W_a = V_a^{-1} A_a^{-1},
+//   K_II^{-1} = (V_x (x) V_y (x) V_z) diag(1 / (lx + ly + lz)) (W_x (x) W_y (x) W_z),
+// i.e. d dense per-axis transforms, a diagonal scaling and d more transforms:
+// plain GEMMs over the coefficient tensor (cuBLAS), with a fused diagonal
+// kernel.  The transforms run in FP32; the operator P = diag(I, K_II^{-1}) they
+// form is applied inside iterative refinement whose residual b - K u is taken
+// by the contraction kernel in FP64 or double-float arithmetic: one correction
+// for pair tensors (FP32 + refinement), `iters` corrections for FP64 tensors.
+// Boundary rows: P copies the residual, so the boundary values and the
+// coupling K_IB they induce are settled by the refinement itself.
+//
+// Set-up (once per context): the 1D pencils are factored and diagonalised in
+// FP64 with cuSOLVER (LU, nonsymmetric eigensolver), then stored as FP32
+// matrices embedded in the axis' full index range.
+#include <cublas_v2.h>
+#include <cusolverDn.h>
+
+#include <cmath>
+#include <cstdio>
+#include <vector>
+
+#include "contract.cuh"
+#include "poisson.h"
+
+namespace igapw {
+
+// ---- contraction instantiations for K u and b - K u (2D and 3D) -------------
+template <int DIM, int W>
+static cudaError_t poisson_mode(const ContractArgs& a, int mode, int cmp, int io, cudaStream_t st) {
+    if (mode == MODE_PK) {
+        if (io == FMT_F64) return pick_tile<DIM, W, double, MODE_PK, FMT_F64>(a, st);
+        return pick_tile<DIM, W, DF, MODE_PK, FMT_PAIR>(a, st);
+    }
+    if (io == FMT_F64) return pick_tile<DIM, W, double, MODE_PRES, FMT_F64>(a, st);
+    if (cmp == FMT_F64) return pick_tile<DIM, W, double, MODE_PRES, FMT_PAIR>(a, st);
+    return pick_tile<DIM, W, DF, MODE_PRES, FMT_PAIR>(a, st);
+}
+
+template <int DIM>
+static cudaError_t poisson_w(const ContractArgs& a, int mode, int cmp, int io, cudaStream_t st) {
+    switch (a.W) {
+        case 3: return poisson_mode<DIM, 3>(a, mode, cmp, io, st);
+        case 5: return poisson_mode<DIM, 5>(a, mode, cmp, io, st);
+        case 7: return poisson_mode<DIM, 7>(a, mode, cmp, io, st);
+        case 9: return poisson_mode<DIM, 9>(a, mode, cmp, io, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_poisson_contract(const ContractArgs& a, int mode, int cmp, int io, cudaStream_t st) {
+    if (mode != MODE_PK && mode != MODE_PRES) return cudaErrorInvalidValue;
+    if (a.dim == 2) return poisson_w<2>(a, mode, cmp, io, st);
+    if (a.dim == 3) return poisson_w<3>(a, mode, cmp, io, st);
+    return cudaErrorInvalidValue;
+}
+
+// ---- elementwise kernels ------------------------------------------------------
+// Grid: (ceil(n_x / 256), n_y, n_z); one thread per coefficient.
+struct Grid3 {
+    int n[3];
+    long long ntot;
+    const int* is_free[3];   // NULL beyond the problem's dimension
+    const float* lam[3];     // NULL beyond the problem's dimension
+};
+
+__device__ __forceinline__ bool grid_index(const Grid3& g, int& x, int& y, int& z, long long& i) {
+    x = blockIdx.x * blockDim.x + threadIdx.x;
+    y = blockIdx.y;
+    z = blockIdx.z;
+    if (x >= g.n[0]) return false;
+    i = ((long long)z * g.n[1] + y) * g.n[0] + x;
+    return true;
+}
+
+__device__ __forceinline__ bool free_at(const Grid3& g, int x, int y, int z) {
+    bool f = g.is_free[0][x] != 0;
+    if (g.is_free[1]) f = f && g.is_free[1][y] != 0;
+    if (g.is_free[2]) f = f && g.is_free[2][z] != 0;
+    return f;
+}
+
+// t /= lx + ly + lz  (spectral domain; boundary entries are zero)
+__global__ void fdm_diag_kernel(Grid3 g, float* t) {
+    int x, y, z;
+    long long i;
+    if (!grid_index(g, x, y, z, i)) return;
+    float s = g.lam[0][x];
+    if (g.lam[1]) s += g.lam[1][y];
+    if (g.lam[2]) s += g.lam[2][z];
+    t[i] = t[i] / s;
+}
+
+// u0 = P r: the transformed value off the boundary, r itself on it
+__global__ void fdm_first_kernel(Grid3 g, const float* t, const float* r, float* u0) {
+    int x, y, z;
+    long long i;
+    if (!grid_index(g, x, y, z, i)) return;
+    u0[i] = free_at(g, x, y, z) ? t[i] : r[i];
+}
+
+// pair output (hi, lo) = u0 + P rho, rounded to nearest as a double-float
+__global__ void fdm_final_pair_kernel(Grid3 g, const float* u0, const float* t, const float* rho, float* out) {
+    int x, y, z;
+    long long i;
+    if (!grid_index(g, x, y, z, i)) return;
+    const float d = free_at(g, x, y, z) ? t[i] : rho[i];
+    float s, e;
+    two_sum(u0[i], d, s, e);
+    out[i] = s;
+    out[i + g.ntot] = e;
+}
+
+__global__ void fdm_to_f32_kernel(Grid3 g, const double* b, float* r) {
+    int x, y, z;
+    long long i;
+    if (!grid_index(g, x, y, z, i)) return;
+    r[i] = (float)b[i];
+}
+
+// u = (first ? 0 : u) + P rho in FP64
+__global__ void fdm_update_f64_kernel(Grid3 g, const float* t, const float* rho, double* u, int first) {
+    int x, y, z;
+    long long i;
+    if (!grid_index(g, x, y, z, i)) return;
+    const double d = (double)(free_at(g, x, y, z) ? t[i] : rho[i]);
+    u[i] = first ? d : u[i] + d;
+}
+
+// ---- set-up ---------------------------------------------------------------------
+namespace {
+
+#define FDM_CUDA(x)                                                                         \
+    do {                                                                                    \
+        cudaError_t e_ = (x);                                                               \
+        if (e_ != cudaSuccess) {                                                            \
+            err = std::string(#x) + ": " + cudaGetErrorString(e_);                          \
+            return e_ == cudaErrorMemoryAllocation ? -3 : -4;                               \
+        }                                                                                   \
+    } while (0)
+#define FDM_SOLVER(x)                                                                       \
+    do {                                                                                    \
+        cusolverStatus_t e_ = (x);                                                          \
+        if (e_ != CUSOLVER_STATUS_SUCCESS) {                                                \
+            err = std::string(#x) + ": cusolver status " + std::to_string((int)e_);         \
+            return -4;                                                                      \
+        }                                                                                   \
+    } while (0)
+#define FDM_BLAS(x)                                                                         \
+    do {                                                                                    \
+        cublasStatus_t e_ = (x);                                                            \
+        if (e_ != CUBLAS_STATUS_SUCCESS) {                                                  \
+            err = std::string(#x) + ": cublas status " + std::to_string((int)e_);           \
+            return -4;                                                                      \
+        }                                                                                   \
+    } while (0)
+
+// Scoped device buffers, solver handle and private stream of one fdm_build
+// call.  Buffers are stream-ordered (cudaMallocAsync / cudaFreeAsync) so that
+// set-up never synchronises the device: other contexts keep running.
+struct Scratch {
+    cudaStream_t ss = nullptr;
+    std::vector<void*> dev;
+    cusolverDnHandle_t solver = nullptr;
+    cusolverDnParams_t params = nullptr;
+    ~Scratch() {
+        for (void* p : dev) cudaFreeAsync(p, ss);
+        if (ss) cudaStreamSynchronize(ss);
+        if (params) cusolverDnDestroyParams(params);
+        if (solver) cusolverDnDestroy(solver);
+        if (ss) cudaStreamDestroy(ss);
+    }
+    template <typename T>
+    cudaError_t alloc(T** p, size_t count) {
+        cudaError_t e = cudaMallocAsync((void**)p, (count ? count : 1) * sizeof(T), ss);
+        if (e == cudaSuccess) dev.push_back(*p);
+        return e;
+    }
+    cudaError_t h2d(void* dst, const void* src, size_t bytes) {
+        return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, ss);
+    }
+    cudaError_t d2h(void* dst, const void* src, size_t bytes) {
+        cudaError_t e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, ss);
+        return e == cudaSuccess ? cudaStreamSynchronize(ss) : e;
+    }
+};
+
+// LU factorisation (in place) followed by X <- A^{-1} X (n x nrhs, column-major).
+int lu_solve(Scratch& S, int64_t n, double* A, int64_t* ipiv, double* X, int64_t nrhs, int* dinfo,
+             std::string& err, const char* what) {
+    size_t dws = 0, hws = 0;
+    FDM_SOLVER(cusolverDnXgetrf_bufferSize(S.solver, S.params, n, n, CUDA_R_64F, A, n, CUDA_R_64F, &dws, &hws));
+    void* dbuf = nullptr;
+    FDM_CUDA(S.alloc((unsigned char**)&dbuf, dws));
+    std::vector<unsigned char> hbuf(hws ? hws : 1);
+    FDM_SOLVER(cusolverDnXgetrf(S.solver, S.params, n, n, CUDA_R_64F, A, n, ipiv, CUDA_R_64F, dbuf, dws,
+                                hbuf.data(), hws, dinfo));
+    int info = 0;
+    FDM_CUDA(S.d2h(&info, dinfo, sizeof info));
+    if (info != 0) {
+        err = std::string(what) + ": singular 1D matrix (getrf info " + std::to_string(info) + ")";
+        return -2;
+    }
+    FDM_SOLVER(cusolverDnXgetrs(S.solver, S.params, CUBLAS_OP_N, n, nrhs, CUDA_R_64F, A, n, ipiv, CUDA_R_64F, X,
+                                n, dinfo));
+    return 0;
+}
+
+int build_axis(FdmState& s, int a, const FdmAxisInput& in, Scratch& S, cublasHandle_t blas, std::string& err) {
+    const int n = in.n, W = in.W;
+    std::vector<int> fr, pos(n, -1);
+    for (int i = 0; i < n; ++i)
+        if (in.is_free[i]) {
+            pos[i] = (int)fr.size();
+            fr.push_back(i);
+        }
+    const int64_t m = (int64_t)fr.size();
+    if (m == 0) {
+        err = "axis " + std::to_string(a) + " has no unknowns";
+        return -1;
+    }
+    // dense interior blocks, column-major: A_I and L_I = -C_I
+    std::vector<double> Ai((size_t)m * m, 0.0), Li((size_t)m * m, 0.0);
+    for (int r = 0; r < m; ++r) {
+        const int i = fr[r];
+        for (int w = 0; w < W; ++w) {
+            const int j = in.fstart[i] + w;
+            if (j < 0 || j >= n || pos[j] < 0) continue;
+            Ai[(size_t)r + (size_t)pos[j] * m] = in.A[(size_t)i * W + w];
+            Li[(size_t)r + (size_t)pos[j] * m] = -in.C[(size_t)i * W + w];
+        }
+    }
+    const size_t mm = (size_t)m * m;
+    double *dLU, *dG, *dV, *dAI, *dB, *dX;
+    int64_t* ipiv;
+    int* dinfo;
+    cuDoubleComplex* dw;
+    FDM_CUDA(S.alloc(&dLU, mm));
+    FDM_CUDA(S.alloc(&dG, mm));
+    FDM_CUDA(S.alloc(&dV, mm));
+    FDM_CUDA(S.alloc(&dAI, mm));
+    FDM_CUDA(S.alloc(&dB, mm));
+    FDM_CUDA(S.alloc(&dX, mm));
+    FDM_CUDA(S.alloc(&ipiv, (size_t)m));
+    FDM_CUDA(S.alloc(&dinfo, 1));
+    FDM_CUDA(S.alloc(&dw, (size_t)m));
+    FDM_CUDA(S.h2d(dLU, Ai.data(), mm * 8));
+    FDM_CUDA(S.h2d(dAI, Ai.data(), mm * 8));
+    FDM_CUDA(S.h2d(dG, Li.data(), mm * 8));
+    // G = A_I^{-1} L_I
+    int rc = lu_solve(S, m, dLU, ipiv, dG, m, dinfo, err, "mass block");
+    if (rc) return rc;
+    // G = V diag(lambda) V^{-1}
+    size_t dws = 0, hws = 0;
+    FDM_SOLVER(cusolverDnXgeev_bufferSize(S.solver, S.params, CUSOLVER_EIG_MODE_NOVECTOR, CUSOLVER_EIG_MODE_VECTOR,
+                                          m, CUDA_R_64F, dG, m, CUDA_C_64F, dw, CUDA_R_64F, nullptr, 1, CUDA_R_64F,
+                                          dV, m, CUDA_R_64F, &dws, &hws));
+    void* dbuf = nullptr;
+    FDM_CUDA(S.alloc((unsigned char**)&dbuf, dws));
+    std::vector<unsigned char> hbuf(hws ? hws : 1);
+    FDM_SOLVER(cusolverDnXgeev(S.solver, S.params, CUSOLVER_EIG_MODE_NOVECTOR, CUSOLVER_EIG_MODE_VECTOR, m,
+                               CUDA_R_64F, dG, m, CUDA_C_64F, dw, CUDA_R_64F, nullptr, 1, CUDA_R_64F, dV, m,
+                               CUDA_R_64F, dbuf, dws, hbuf.data(), hws, dinfo));
+    int info = 0;
+    FDM_CUDA(S.d2h(&info, dinfo, sizeof info));
+    if (info != 0) {
+        err = "eigensolver did not converge (geev info " + std::to_string(info) + ")";
+        return -4;
+    }
+    std::vector<cuDoubleComplex> lam_c((size_t)m);
+    FDM_CUDA(S.d2h(lam_c.data(), dw, (size_t)m * sizeof(cuDoubleComplex)));
+    double lmax = 0.0, imax = 0.0, lmin = INFINITY;
+    for (auto z : lam_c) {
+        lmax = std::fmax(lmax, std::fabs(z.x));
+        lmin = std::fmin(lmin, z.x);
+        imax = std::fmax(imax, std::fabs(z.y));
+    }
+    if (imax > 1e-9 * lmax || !(lmin > 0.0)) {
+        err = "1D pencil spectrum not real and positive (max |imag| " + std::to_string(imax) + ", min real " +
+              std::to_string(lmin) + ")";
+        return -1;
+    }
+    // W = (A_I V)^{-1} = V^{-1} A_I^{-1}
+    const double one = 1.0, zero = 0.0;
+    FDM_BLAS(cublasDgemm(blas, CUBLAS_OP_N, CUBLAS_OP_N, (int)m, (int)m, (int)m, &one, dAI, (int)m, dV, (int)m,
+                         &zero, dB, (int)m));
+    std::vector<double> I(mm, 0.0);
+    for (int64_t k = 0; k < m; ++k) I[(size_t)k + (size_t)k * m] = 1.0;
+    FDM_CUDA(S.h2d(dX, I.data(), mm * 8));
+    rc = lu_solve(S, m, dB, ipiv, dX, m, dinfo, err, "eigenvector block");
+    if (rc) return rc;
+    std::vector<double> V(mm), X(mm);
+    FDM_CUDA(S.d2h(V.data(), dV, mm * 8));
+    FDM_CUDA(S.d2h(X.data(), dX, mm * 8));
+    // check a few eigenpairs against the pencil: |L v - lambda A v| <= tol |L| |v|
+    double lnorm = 0.0;
+    for (double v : Li) lnorm = std::fmax(lnorm, std::fabs(v));
+    for (int t = 0; t < 4; ++t) {
+        const int64_t k = (t * (m - 1)) / 3;
+        double worst = 0.0;
+        for (int64_t r = 0; r < m; ++r) {
+            double lv = 0.0, av = 0.0;
+            for (int64_t c = 0; c < m; ++c) {
+                lv += Li[(size_t)r + (size_t)c * m] * V[(size_t)c + (size_t)k * m];
+                av += Ai[(size_t)r + (size_t)c * m] * V[(size_t)c + (size_t)k * m];
+            }
+            worst = std::fmax(worst, std::fabs(lv - lam_c[k].x * av));
+        }
+        if (!(worst <= 1e-8 * lnorm * (double)m)) {
+            err = "inaccurate eigenpair " + std::to_string(k) + " (residual " + std::to_string(worst) + ")";
+            return -4;
+        }
+    }
+    // embed in the full index range as FP32
+    std::vector<float> Wf((size_t)n * n, 0.f), Vf((size_t)n * n, 0.f), lf(n, 1.f);
+    for (int64_t k = 0; k < m; ++k) {
+        lf[fr[k]] = (float)lam_c[k].x;
+        for (int64_t r = 0; r < m; ++r) {
+            Vf[(size_t)fr[r] + (size_t)fr[k] * n] = (float)V[(size_t)r + (size_t)k * m];
+            Wf[(size_t)fr[k] + (size_t)fr[r] * n] = (float)X[(size_t)k + (size_t)r * m];
+        }
+    }
+    for (float** p : {&s.Wm[a], &s.Vm[a]}) {
+        FDM_CUDA(cudaMalloc((void**)p, (size_t)n * n * sizeof(float)));
+        s.allocs.push_back(*p);
+    }
+    FDM_CUDA(cudaMalloc((void**)&s.lam[a], (size_t)n * sizeof(float)));
+    s.allocs.push_back(s.lam[a]);
+    FDM_CUDA(S.h2d(s.Wm[a], Wf.data(), Wf.size() * 4));
+    FDM_CUDA(S.h2d(s.Vm[a], Vf.data(), Vf.size() * 4));
+    FDM_CUDA(S.h2d(s.lam[a], lf.data(), lf.size() * 4));
+    FDM_CUDA(cudaStreamSynchronize(S.ss));   // host vectors go out of scope
+    return 0;
+}
+
+}  // namespace
+
+void fdm_release(FdmState& s) {
+    for (void* p : s.allocs) cudaFree(p);
+    s.allocs.clear();
+    if (s.blas) cublasDestroy(s.blas);
+    s.blas = nullptr;
+    for (int a = 0; a < 3; ++a) s.Wm[a] = s.Vm[a] = s.lam[a] = nullptr;
+}
+
+int fdm_build(FdmState& s, int dim, const FdmAxisInput* ax, const int* const* is_free_dev, bool tensor,
+              cudaStream_t st, std::string& err) {
+    fdm_release(s);
+    s.dim = dim;
+    s.tensor = tensor;
+    for (int a = 0; a < 3; ++a) {
+        s.n[a] = a < dim ? ax[a].n : 1;
+        s.is_free[a] = a < dim ? is_free_dev[a] : nullptr;
+    }
+    FDM_CUDA(cudaStreamSynchronize(st));   // the folded tables are final
+    FDM_BLAS(cublasCreate(&s.blas));
+    Scratch S;
+    FDM_CUDA(cudaStreamCreateWithFlags(&S.ss, cudaStreamNonBlocking));
+    FDM_SOLVER(cusolverDnCreate(&S.solver));
+    FDM_SOLVER(cusolverDnCreateParams(&S.params));
+    FDM_SOLVER(cusolverDnSetStream(S.solver, S.ss));
+    FDM_BLAS(cublasSetStream(s.blas, S.ss));
+    for (int a = 0; a < dim; ++a) {
+        int rc = build_axis(s, a, ax[a], S, s.blas, err);
+        if (rc) return rc;
+    }
+    FDM_CUDA(cudaStreamSynchronize(S.ss));
+    FDM_BLAS(cublasSetStream(s.blas, st));
+    if (tensor) FDM_BLAS(cublasSetMathMode(s.blas, CUBLAS_FP32_EMULATED_BF16X9_MATH));
+    return 0;
+}
+
+// ---- solve ---------------------------------------------------------------------
+namespace {
+
+// out = M applied along axis a of the (n_z, n_y, n_x) tensor `in`
+int gemm_axis(FdmState& s, int a, const float* M, const float* in, float* out, std::string& err) {
+    const int nx = s.n[0], ny = s.n[1], nz = s.n[2];
+    const float one = 1.f, zero = 0.f;
+    const cublasComputeType_t ct = s.tensor ? CUBLAS_COMPUTE_32F_EMULATED_16BFX9 : CUBLAS_COMPUTE_32F;
+    if (a == 0) {
+        FDM_BLAS(cublasGemmEx(s.blas, CUBLAS_OP_N, CUBLAS_OP_N, nx, ny * nz, nx, &one, M, CUDA_R_32F, nx, in,
+                              CUDA_R_32F, nx, &zero, out, CUDA_R_32F, nx, ct, CUBLAS_GEMM_DEFAULT));
+    } else if (a == 1) {
+        FDM_BLAS(cublasGemmStridedBatchedEx(s.blas, CUBLAS_OP_N, CUBLAS_OP_T, nx, ny, ny, &one, in, CUDA_R_32F, nx,
+                                            (long long)nx * ny, M, CUDA_R_32F, ny, 0, &zero, out, CUDA_R_32F, nx,
+                                            (long long)nx * ny, nz, ct, CUBLAS_GEMM_DEFAULT));
+    } else {
+        FDM_BLAS(cublasGemmEx(s.blas, CUBLAS_OP_N, CUBLAS_OP_T, nx * ny, nz, nz, &one, in, CUDA_R_32F, nx * ny, M,
+                              CUDA_R_32F, nz, &zero, out, CUDA_R_32F, nx * ny, ct, CUBLAS_GEMM_DEFAULT));
+    }
+    return 0;
+}
+
+Grid3 grid_of(const FdmState& s, long long ntot) {
+    Grid3 g{};
+    for (int a = 0; a < 3; ++a) {
+        g.n[a] = s.n[a];
+        g.is_free[a] = s.is_free[a];
+        g.lam[a] = a < s.dim ? s.lam[a] : nullptr;
+    }
+    g.ntot = ntot;
+    return g;
+}
+
+dim3 grid_dims(const Grid3& g) { return dim3((g.n[0] + 255) / 256, g.n[1], g.n[2]); }
+
+// t1 = P-transform of r off the boundary (zero on it): W's, 1/(sum lambda), V's
+int apply_fdm(FdmState& s, const Grid3& g, const float* r, float* t0, float* t1, cudaStream_t st,
+              std::string& err) {
+    const float* cur = r;
+    int step = 0;
+    for (int a = 0; a < s.dim; ++a, ++step) {
+        float* out = (step % 2 == 0) ? t0 : t1;
+        int rc = gemm_axis(s, a, s.Wm[a], cur, out, err);
+        if (rc) return rc;
+        cur = out;
+    }
+    fdm_diag_kernel<<<grid_dims(g), 256, 0, st>>>(g, const_cast<float*>(cur));
+    FDM_CUDA(cudaGetLastError());
+    for (int a = 0; a < s.dim; ++a, ++step) {
+        float* out = (step % 2 == 0) ? t0 : t1;
+        int rc = gemm_axis(s, a, s.Vm[a], cur, out, err);
+        if (rc) return rc;
+        cur = out;
+    }
+    return 0;   // 2 dim transforms: the last one wrote t1
+}
+
+}  // namespace
+
+int fdm_solve(FdmState& s, const ContractArgs& ca, const void* b, void* u, bool fp64, int iters, float* t0,
+              float* t1, float* rho, float* u0, bool pair_fp64_residual, cudaStream_t st, std::string& err) {
+    FDM_BLAS(cublasSetStream(s.blas, st));
+    const Grid3 g = grid_of(s, ca.ntot);
+    const dim3 gd = grid_dims(g);
+    if (!fp64) {
+        const float* bhi = (const float*)b;
+        int rc = apply_fdm(s, g, bhi, t0, t1, st, err);
+        if (rc) return rc;
+        fdm_first_kernel<<<gd, 256, 0, st>>>(g, t1, bhi, u0);
+        FDM_CUDA(cudaGetLastError());
+        ContractArgs a = ca;
+        a.u = u0;
+        a.r = b;
+        a.out = rho;
+        a.alpha = 0.0;
+        a.beta = -1.0;
+        FDM_CUDA(launch_poisson_contract(a, MODE_PRES, pair_fp64_residual ? FMT_F64 : FMT_PAIR, FMT_PAIR, st));
+        rc = apply_fdm(s, g, rho, t0, t1, st, err);
+        if (rc) return rc;
+        fdm_final_pair_kernel<<<gd, 256, 0, st>>>(g, u0, t1, rho, (float*)u);
+        FDM_CUDA(cudaGetLastError());
+        return 0;
+    }
+    fdm_to_f32_kernel<<<gd, 256, 0, st>>>(g, (const double*)b, rho);
+    FDM_CUDA(cudaGetLastError());
+    for (int it = 0; it <= iters; ++it) {
+        int rc = apply_fdm(s, g, rho, t0, t1, st, err);
+        if (rc) return rc;
+        fdm_update_f64_kernel<<<gd, 256, 0, st>>>(g, t1, rho, (double*)u, it == 0);
+        FDM_CUDA(cudaGetLastError());
+        if (it == iters) break;
+        ContractArgs a = ca;
+        a.u = u;
+        a.r = b;
+        a.out = rho;
+        a.alpha = 0.0;
+        a.beta = -1.0;
+        FDM_CUDA(launch_poisson_contract(a, MODE_PRES, FMT_F64, FMT_F64, st));
+    }
+    return 0;
+}
+
+}  // namespace igapw

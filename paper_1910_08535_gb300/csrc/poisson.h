@@ -1,0 +1,52 @@
+// Multi-D Poisson solve by fast diagonalisation (poisson.cu <-> api.cu).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "kernels.h"
+
+typedef struct cublasContext* cublasHandle_t;
+
+namespace igapw {
+
+// Host view of one axis' folded 1D tables (window layout, n x W).
+struct FdmAxisInput {
+    int n = 0, W = 0;
+    std::vector<double> A, C;        // int T_i B_j, int T_i B_j'' (Dirichlet rows: A identity, C 0)
+    std::vector<int> fstart, is_free;
+};
+
+// Per-axis spectral data, embedded in the full index range [0, n): unknown
+// k of the axis' free set sits at index free[k]; boundary rows and columns
+// of W and V are zero and the boundary eigenvalues are 1 (never divided into
+// a non-zero value).
+struct FdmState {
+    int dim = 0;
+    int n[3] = {1, 1, 1};
+    float* Wm[3] = {nullptr, nullptr, nullptr};   // n x n column-major, V^{-1} A_I^{-1}
+    float* Vm[3] = {nullptr, nullptr, nullptr};   // n x n column-major, V
+    float* lam[3] = {nullptr, nullptr, nullptr};  // n eigenvalues of A_I^{-1} L_I
+    const int* is_free[3] = {nullptr, nullptr, nullptr};
+    cublasHandle_t blas = nullptr;
+    bool tensor = false;                           // FP32 GEMMs emulated on the bf16 tensor pipe
+    std::vector<void*> allocs;
+};
+
+// Builds the spectral data of every axis (FP64 LU and eigendecomposition on
+// the device, then FP32 copies).  Returns 0, or a message in err.
+int fdm_build(FdmState& s, int dim, const FdmAxisInput* ax, const int* const* is_free_dev, bool tensor,
+              cudaStream_t st, std::string& err);
+void fdm_release(FdmState& s);
+
+// Poisson solve K u = b.  Scratch: t0, t1, rho (ntot floats each) and, for
+// pair tensors, u0 (ntot floats).  b and u are pair tensors (fp64 == false)
+// or double tensors (fp64 == true; `iters` refinement steps).
+int fdm_solve(FdmState& s, const ContractArgs& ca, const void* b, void* u, bool fp64, int iters, float* t0,
+              float* t1, float* rho, float* u0, bool pair_fp64_residual, cudaStream_t st, std::string& err);
+
+// r = K u (MODE_PK) or rho = r - K u (MODE_PRES) through the contraction kernel.
+cudaError_t launch_poisson_contract(const ContractArgs& a, int mode, int cmp, int io, cudaStream_t st);
+
+}  // namespace igapw

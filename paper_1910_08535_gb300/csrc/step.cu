@@ -1,365 +1,28 @@
-// The explicit heat step in split form (one kernel launch per axis).
-//
-// Each step of Sec. 4.2, Eq. (6) solves (Mz (x) My (x) Mx) u' = T(u + dt Lap u)
-// with M = T B the tested mass and the tested Laplacian
-//   T Lap u = (C_x (x) A_y (x) A_z + A_x (x) C_y (x) A_z + A_x (x) A_y (x) C_z) u,
-// A = int T_i B_j, C = int T_i B_j'' per axis (PW cells or B-spline tests).
-// Because the mass is the Kronecker product of the per-axis A, the factors of
-// the other axes cancel against their inverses:
-//   u' = u + dt * sum_a (A_a^{-1} C_a applied along axis a) u.
-// So one step is, for every axis a and every line along a:
-//   g = C_a u (tested Laplacian along the line), w = A_a^{-1} g (banded solve),
-//   accumulated as u' = u + dt (w_x + w_y + w_z).
-// This is the same discrete scheme as RHS-then-solve (the same M and T); only
-// the rounding order differs.  The line never leaves the block: contraction,
-// solve, residual and correction run on a shared-memory copy of the line.
-//
-// FP32-pair mode: g in double-float; w0 = A^{-1} g_hi in FP32; residual
-// rho = g - A w0 in double-float; delta = A^{-1} rho in FP32; w = w0 + delta.
-// FP64 mode: g and the solve in FP64.
-#include <algorithm>
-#include <type_traits>
-
-#include "common.cuh"
+// Split-step dispatch over value type and degree; the kernel is in step.cuh,
+// instantiated by step_f64_p*.cu and step_df_p*.cu (compiled in parallel).
 #include "kernels.h"
-#include "linesolve.cuh"
 
 namespace igapw {
 
-namespace {
-
-__host__ __device__ constexpr size_t align16(size_t b) { return (b + 15) & ~(size_t)15; }
-
-template <typename VT>
-struct StepTypes;
-template <>
-struct StepTypes<double> {
-    using S = double;   // solve type
-};
-template <>
-struct StepTypes<DF> {
-    using S = float;
-};
-
-__device__ __forceinline__ DF ld_tab(const TableSet& t, int idx, DF) {
-    const float2 v = t.df[idx];
-    return DF{v.x, v.y};
-}
-__device__ __forceinline__ double ld_tab(const TableSet& t, int idx, double) { return t.d[idx]; }
-
-// Global value of the state / accumulator tensor.
-__device__ __forceinline__ DF ld_state(const void* p, long long g, long long ntot, DF) {
-    const float* f = (const float*)p;
-    return DF{f[g], f[g + ntot]};
-}
-__device__ __forceinline__ double ld_state(const void* p, long long g, long long, double) {
-    return ((const double*)p)[g];
-}
-__device__ __forceinline__ void st_state(void* p, long long g, long long ntot, DF v) {
-    ((float*)p)[g] = v.hi;
-    ((float*)p)[g + ntot] = v.lo;
-}
-__device__ __forceinline__ void st_state(void* p, long long g, long long, double v) { ((double*)p)[g] = v; }
-
-}  // namespace
-
-// MODE: 0 FIRST (acc = u + dt w), 1 MID (acc += dt w), 2 LAST (u = acc + dt w),
-// 3 ONLY (u = u + dt w).  XL: lines along x (contiguous) or along y/z.
-template <typename VT, int KP, int W, int MODE, bool XL>
-__global__ void __launch_bounds__(256) axis_step_kernel(const AxisStepArgs a) {
-    using TS = typename StepTypes<VT>::S;
-    constexpr bool DFM = std::is_same<VT, DF>::value;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ int bnd[33];
-    const AxisDev& AX = a.ax;
-    const LineSys<TS>& LS = *(DFM ? (const LineSys<TS>*)&AX.ls32 : (const LineSys<TS>*)&AX.ls64);
-    const int n = AX.n;
-    const int nx = a.n[0], ny = a.n[1];
-    const int NL = XL ? a.lines_per_block : 32;
-
-    // ---- shared memory carve-up ------------------------------------------
-    // every segment starts on a 16-byte boundary (8-byte cp.async targets)
-    TS* tabs = reinterpret_cast<TS*>(smem_raw);
-    unsigned char* p = smem_raw + align16(table_elems<TS, KP>(n) * sizeof(TS));
-    VT* Ct = reinterpret_cast<VT*>(p);
-    VT* At = Ct + n * W;
-    p += align16((size_t)2 * n * W * sizeof(VT));
-    int* fs = reinterpret_cast<int*>(p);
-    p += align16((size_t)n * sizeof(int));
-    // lines carry W zero rows past n, so the contraction windows need no guards
-    const int nr = n + W;
-    const int pitch = XL ? (nr | 1) : NL + 1;
-    const int st = XL ? 1 : pitch;      // row stride within a line
-    const int lst = XL ? pitch : 1;     // line stride
-    const int cap = XL ? NL * pitch : nr * pitch;
-    VT* G = reinterpret_cast<VT*>(p);               // g (and, FP64, the solve buffer)
-    VT* Ub = G + cap;                               // u during the contraction
-    TS* X = reinterpret_cast<TS*>(Ub);              // FP32 pair mode: w0 ...
-    TS* R = X + cap;                                //  ... and the residual / correction
-
-    const SolveSmem<TS> S = stage_tables<TS, KP>(LS, tabs);
-    for (int e = threadIdx.x; e < n * W; e += blockDim.x) {
-        if constexpr (DFM) {
-            cp_async8(Ct + e, AX.C.df + e);
-            cp_async8(At + e, AX.A.df + e);
-        } else {
-            cp_async8(Ct + e, AX.C.d + e);
-            cp_async8(At + e, AX.A.d + e);
-        }
-    }
-    for (int e = threadIdx.x; e < n; e += blockDim.x) cp_async4(fs + e, AX.fstart + e);
-    if (threadIdx.x < 33) bnd[threadIdx.x] = LS.b[threadIdx.x];
-
-    // ---- which lines: global index of (line l, row i) ---------------------
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    long long l0 = 0, os = 0, rs = 0;
-    int nl, x0 = 0;
-    if (XL) {
-        const long long nlines = (long long)a.n[1] * a.n[2];
-        l0 = (long long)blockIdx.x * NL;
-        nl = (int)min((long long)NL, nlines - l0);
-    } else {
-        x0 = blockIdx.x * NL;
-        nl = min(NL, nx - x0);
-        if (a.axis == 1) { os = (long long)ny * nx; rs = nx; }
-        else { os = nx; rs = (long long)nx * ny; }
-    }
-    auto gidx = [&](int l, int i) -> long long {
-        if (XL) return (l0 + l) * n + i;
-        return (long long)blockIdx.y * os + (long long)i * rs + x0 + l;
-    };
-
-    // asynchronous copy of a state / accumulator tensor's lines into buf
-    auto stage = [&](VT* buf, const void* src) {
-        if (XL) {
-            for (int l = warp; l < nl; l += nw)
-                for (int i = lane; i < n; i += 32) {
-                    const long long g = gidx(l, i);
-                    VT* d = buf + l * pitch + i;
-                    if constexpr (DFM) {
-                        cp_async4(&d->hi, (const float*)src + g);
-                        cp_async4(&d->lo, (const float*)src + g + a.ntot);
-                    } else {
-                        cp_async8(d, (const double*)src + g);
-                    }
-                }
-        } else {
-            for (int i = warp; i < n; i += nw) {
-                VT* d = buf + i * pitch + lane;
-                if (lane < nl) {
-                    const long long g = gidx(lane, i);
-                    if constexpr (DFM) {
-                        cp_async4(&d->hi, (const float*)src + g);
-                        cp_async4(&d->lo, (const float*)src + g + a.ntot);
-                    } else {
-                        cp_async8(d, (const double*)src + g);
-                    }
-                } else {
-                    *d = VT{};
-                }
-            }
-        }
-    };
-
-    // visits every staged (line, row) of the block, rows [r0, r1), without divisions
-    auto for_each = [&](int r0, int r1, auto&& f) {
-        if (XL) {
-            for (int l = warp; l < nl; l += nw)
-                for (int i = r0 + lane; i < r1; i += 32) f(l, i);
-        } else {
-            for (int i = r0 + warp; i < r1; i += nw) f(lane, i);
-        }
-    };
-
-    // ---- P0: stage u ---------------------------------------------------------
-    stage(Ub, a.u);
-    for_each(n, nr, [&](int l, int i) { Ub[i * st + l * lst] = VT{}; });
-    cp_async_wait_all();
-    __syncthreads();
-
-    // ---- P1: g = C u along the line (compensated in pair mode) --------------
-    for_each(0, n, [&](int l, int i) {
-        const VT* ub = Ub + fs[i] * st + l * lst;
-        const VT* ct = Ct + i * W;
-        if constexpr (DFM) {
-            DFAcc acc;
-            acc.init();
-#pragma unroll
-            for (int w = 0; w < W; ++w) acc.add_prod(ct[w], ub[w * st]);
-            G[i * st + l * lst] = acc.result();
-        } else {
-            double s = 0.0;
-#pragma unroll
-            for (int w = 0; w < W; ++w) s = fma(ct[w], ub[w * st], s);
-            G[i * st + l * lst] = s;
-        }
-    });
-    __syncthreads();
-
-    const int P = LS.P;
-    const int groups = 32 / P;
-    const int grp = lane / P, k = lane - grp * P;
-    const int nlines_b = XL ? nl : NL;   // lines per group set: groups = 32 / P
-    if constexpr (DFM) {
-        // ---- P2: w0 = A^{-1} g_hi (FP32) ------------------------------------
-        for_each(0, nr, [&](int l, int i) { X[i * st + l * lst] = i < n ? G[i * st + l * lst].hi : 0.f; });
-        __syncthreads();
-        for (int base = warp * groups; base < nlines_b; base += nw * groups) {
-            const int first = base + grp;
-            line_solve<TS, KP, 1>(X + min(first, nlines_b) * lst, st, lst, first < nlines_b ? 1 : 0, S, P, bnd,
-                                  k, n);
-        }
-        __syncthreads();
-        // ---- P3: rho = g - A w0 (double-float) ------------------------------
-        for_each(0, n, [&](int l, int i) {
-            const TS* xw = X + fs[i] * st + l * lst;
-            const VT* at = At + i * W;
-            DFAcc acc;
-            const DF g = G[i * st + l * lst];
-            acc.s = g.hi;
-            acc.c = g.lo;
-#pragma unroll
-            for (int w = 0; w < W; ++w) acc.add_prod_f(DF{-at[w].hi, -at[w].lo}, xw[w * st]);
-            R[i * st + l * lst] = acc.result().hi;
-        });
-        __syncthreads();
-        // g is dead: prefetch the tensor the update adds to into G meanwhile
-        stage(G, (MODE == 0 || MODE == 3) ? a.u : a.acc);
-        // ---- P4: delta = A^{-1} rho (FP32) ----------------------------------
-        for (int base = warp * groups; base < nlines_b; base += nw * groups) {
-            const int first = base + grp;
-            line_solve<TS, KP, 1>(R + min(first, nlines_b) * lst, st, lst, first < nlines_b ? 1 : 0, S, P, bnd,
-                                  k, n);
-        }
-        cp_async_wait_all();
-        __syncthreads();
-    } else {
-        // u is dead: prefetch the tensor the update adds to into Ub meanwhile
-        stage(Ub, (MODE == 0 || MODE == 3) ? a.u : a.acc);
-        for (int base = warp * groups; base < nlines_b; base += nw * groups) {
-            const int first = base + grp;
-            line_solve<TS, KP, 1>(reinterpret_cast<TS*>(G) + min(first, nlines_b) * lst, st, lst,
-                                  first < nlines_b ? 1 : 0, S, P, bnd, k, n);
-        }
-        cp_async_wait_all();
-        __syncthreads();
-    }
-
-    // ---- P5: accumulate dt * w ---------------------------------------------
-    const VT dtv = [&] {
-        if constexpr (DFM) {
-            DF d;
-            split_double(a.dt, d.hi, d.lo);
-            return d;
-        } else {
-            return a.dt;
-        }
-    }();
-    unsigned bad = 0;
-    auto finish = [&](int l, int i) {
-        const long long g = gidx(l, i);
-        VT w;
-        if constexpr (DFM) {
-            float hi, lo;
-            two_sum(X[i * st + l * lst], R[i * st + l * lst], hi, lo);
-            w = DF{hi, lo};
-        } else {
-            w = G[i * st + l * lst];
-        }
-        const VT base = DFM ? G[i * st + l * lst] : Ub[i * st + l * lst];
-        VT r;
-        if constexpr (DFM) {
-            DFAcc acc;
-            acc.s = base.hi;
-            acc.c = base.lo;
-            acc.add_prod(dtv, w);
-            r = acc.result();
-            if (!isfinite(r.hi)) bad = 1;
-        } else {
-            r = fma(dtv, w, base);
-            if (!isfinite(r)) bad = 1;
-        }
-        if (MODE == 0 || MODE == 1) st_state(a.acc, g, a.ntot, r);
-        else st_state(a.u_out, g, a.ntot, r);
-    };
-    if (XL) {
-        for (int l = warp; l < nl; l += nw)
-            for (int i = lane; i < n; i += 32) finish(l, i);
-    } else {
-        for (int i = warp; i < n; i += nw)
-            if (lane < nl) finish(lane, i);
-    }
-    if (bad && a.status) atomicOr(a.status, STATUS_NONFINITE);
-}
-
-template <typename VT, int KP, int W, int MODE>
-static cudaError_t run_axis_step(const AxisStepArgs& a0, cudaStream_t st) {
-    using TS = typename StepTypes<VT>::S;
-    AxisStepArgs a = a0;
-    const int n = a.ax.n;
-    const bool xl = a.axis == 0;
-    const long long nlines = (long long)a.n[1] * a.n[2];
-    int lim = 0, dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&lim, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    auto smem_for = [&](int nl) {
-        const int cap = xl ? nl * ((n + W) | 1) : (n + W) * (32 + 1);
-        return align16(table_elems<TS, KP>(n) * sizeof(TS)) + align16((size_t)2 * n * W * sizeof(VT)) +
-               align16((size_t)n * sizeof(int)) + (size_t)2 * cap * sizeof(VT);
-    };
-    int NL = xl ? (int)std::min<long long>(32, nlines) : 32;
-    while (xl && NL > 1 && (int)smem_for(NL) > lim) NL = (NL + 1) / 2;
-    a.lines_per_block = NL;
-    const size_t sm = smem_for(NL);
-    if ((int)sm > lim) return cudaErrorInvalidValue;
-    if (xl) {
-        auto k = axis_step_kernel<VT, KP, W, MODE, true>;
-        if (sm > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        k<<<(unsigned)((nlines + NL - 1) / NL), 256, sm, st>>>(a);
-    } else {
-        auto k = axis_step_kernel<VT, KP, W, MODE, false>;
-        if (sm > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        const int outer = a.axis == 1 ? a.n[2] : a.n[1];
-        dim3 grid((a.n[0] + 31) / 32, outer);
-        k<<<grid, 256, sm, st>>>(a);
-    }
-    return cudaGetLastError();
-}
-
-template <typename VT, int KP, int W>
-static cudaError_t pick_mode(const AxisStepArgs& a, int mode, cudaStream_t st) {
-    switch (mode) {
-        case 0: return run_axis_step<VT, KP, W, 0>(a, st);
-        case 1: return run_axis_step<VT, KP, W, 1>(a, st);
-        case 2: return run_axis_step<VT, KP, W, 2>(a, st);
-        case 3: return run_axis_step<VT, KP, W, 3>(a, st);
-    }
-    return cudaErrorInvalidValue;
-}
-
-template <typename VT, int KP>
-static cudaError_t pick_w(const AxisStepArgs& a, int mode, cudaStream_t st) {
-    switch (a.W) {
-        case 3: return pick_mode<VT, KP, 3>(a, mode, st);
-        case 5: return pick_mode<VT, KP, 5>(a, mode, st);
-        case 7: return pick_mode<VT, KP, 7>(a, mode, st);
-        case 9: return pick_mode<VT, KP, 9>(a, mode, st);
-    }
-    return cudaErrorInvalidValue;
-}
+cudaError_t launch_axis_step_f64_p2(const AxisStepArgs& a, int mode, cudaStream_t st);
+cudaError_t launch_axis_step_f64_p3(const AxisStepArgs& a, int mode, cudaStream_t st);
+cudaError_t launch_axis_step_f64_p4(const AxisStepArgs& a, int mode, cudaStream_t st);
+cudaError_t launch_axis_step_df_p2(const AxisStepArgs& a, int mode, cudaStream_t st);
+cudaError_t launch_axis_step_df_p3(const AxisStepArgs& a, int mode, cudaStream_t st);
+cudaError_t launch_axis_step_df_p4(const AxisStepArgs& a, int mode, cudaStream_t st);
 
 cudaError_t launch_axis_step(const AxisStepArgs& a, int mode, bool fp64, int p, cudaStream_t st) {
     if (fp64) {
         switch (p) {
-            case 2: return pick_w<double, 2>(a, mode, st);
-            case 3: return pick_w<double, 3>(a, mode, st);
-            case 4: return pick_w<double, 4>(a, mode, st);
+            case 2: return launch_axis_step_f64_p2(a, mode, st);
+            case 3: return launch_axis_step_f64_p3(a, mode, st);
+            case 4: return launch_axis_step_f64_p4(a, mode, st);
         }
     } else {
         switch (p) {
-            case 2: return pick_w<DF, 2>(a, mode, st);
-            case 3: return pick_w<DF, 3>(a, mode, st);
-            case 4: return pick_w<DF, 4>(a, mode, st);
+            case 2: return launch_axis_step_df_p2(a, mode, st);
+            case 3: return launch_axis_step_df_p3(a, mode, st);
+            case 4: return launch_axis_step_df_p4(a, mode, st);
         }
     }
     return cudaErrorInvalidValue;

@@ -1,0 +1,10 @@
+// Split-step axis kernels: double-float pair values, degree 3.
+#include "step.cuh"
+
+namespace igapw {
+
+cudaError_t launch_axis_step_df_p3(const AxisStepArgs& a, int mode, cudaStream_t st) {
+    return pick_w<DF, 3>(a, mode, st);
+}
+
+}  // namespace igapw

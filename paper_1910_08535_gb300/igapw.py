@@ -21,7 +21,7 @@ IGAPW_GALERKIN, IGAPW_PWCONST = 0, 1
 IGAPW_BC_NONE, IGAPW_BC_DIRICHLET0 = 0, 1
 IGAPW_FP64, IGAPW_FP32_REFINE = 0, 1
 IGAPW_OP_MASS, IGAPW_OP_LAPLACE, IGAPW_OP_HEAT, IGAPW_OP_POISSON = 0, 1, 2, 3
-IGAPW_FLAG_FP64_RESIDUAL, IGAPW_FLAG_STEP_RHS_SOLVE = 1, 2
+IGAPW_FLAG_FP64_RESIDUAL, IGAPW_FLAG_STEP_RHS_SOLVE, IGAPW_FLAG_FDM_BF16X9 = 1, 2, 4
 
 TESTS = {'galerkin': IGAPW_GALERKIN, 'pw': IGAPW_PWCONST}
 BCS = {'none': IGAPW_BC_NONE, 'dirichlet0': IGAPW_BC_DIRICHLET0}

@@ -75,6 +75,23 @@ def tensor_samples(points, fn_list):
     return out
 
 
+def sine_product_source(points, k):
+    """f = pi^2 (sum_a k_a^2) prod_a sin(k_a pi x_a) on the tensor grid of the
+    1D point sets: the source of u = prod_a sin(k_a pi x_a) for -Lap u = f."""
+    fns = tuple((lambda x, kk=kk: np.sin(kk * np.pi * x)) for kk in k)
+    return np.pi ** 2 * sum(kk * kk for kk in k) * tensor_samples(points, [fns])
+
+
+def sine_product_exact(k):
+    """u = prod_a sin(k_a pi x_a) on coordinate arrays (x first)."""
+    def u(coords):
+        r = 1.0
+        for a, x in enumerate(coords):
+            r = r * np.sin(k[a] * np.pi * x)
+        return r
+    return u
+
+
 def initial_state(name, seed=0):
     w = WORKLOADS[name]
     n = w['n_elem'] + w['degree']
