@@ -31,7 +31,9 @@
  *   - Tensors are dense, C-ordered, x fastest: shape (n_z, n_y, n_x) in 3D,
  *     (n_y, n_x) in 2D, (n_x) in 1D, with n_a = N_{e,a} + p.  Device pointers
  *     must be 16-byte aligned and are owned by the caller; the library never
- *     frees or reallocates them.
+ *     frees or reallocates them.  The library's own device buffers are
+ *     stream-ordered allocations on the context stream (cudaMallocAsync), so
+ *     creating or destroying a context does not synchronise the device.
  *   - Precision IGAPW_FP64: coefficient and RHS tensors are double.
  *     Precision IGAPW_FP32_REFINE: coefficient and RHS tensors are double-float
  *     pairs stored as two consecutive float planes, hi then lo: a float buffer
@@ -160,11 +162,12 @@ int igapw_rhs_source(igapw_ctx* ctx, const void* f_dev, void* b_dev);
 
 /* Allocation-free variant of igapw_rhs_source (the paper has no counterpart:
  * this is a deployment aid).  igapw_rhs_source allocates the two intermediate
- * tensors of its axis-by-axis passes with cudaMalloc on its first call for a
- * context; callers that cannot let the library allocate there (hosts that
- * reserve all device memory up front, schedulers admitting work against a
- * fixed device-memory budget, latency-critical loops that cannot take
- * cudaMalloc's implicit synchronisation) call this instead.  It computes the
+ * tensors of its axis-by-axis passes on its first call for a context (a
+ * stream-ordered allocation after a wait for the context stream); callers
+ * that cannot let the library allocate there (hosts that reserve all device
+ * memory up front, schedulers admitting work against a fixed device-memory
+ * budget, latency-critical loops that cannot take that wait) call this
+ * instead.  It computes the
  * same b into the caller's b_dev, taking its intermediates from one static
  * device array of IGAPW_NOALLOC_SCRATCH_BYTES that every GPU loading the
  * library holds until exit; it calls no allocating routine.

@@ -25,9 +25,15 @@ def nvcc():
     return path
 
 
+def _extra():
+    """Extra nvcc flags from IGAPW_NVCC_EXTRA (e.g. -DIGAPW_BOUNDS_CHECK for a
+    debug build with device-side index checks)."""
+    return os.environ.get('IGAPW_NVCC_EXTRA', '').split()
+
+
 def _compile(src):
     out = os.path.join(OBJ, os.path.splitext(src)[0] + '.o')
-    cmd = [nvcc(), *ARCH, *FLAGS, '-c', os.path.join(CSRC, src), '-o', out]
+    cmd = [nvcc(), *ARCH, *FLAGS, *_extra(), '-c', os.path.join(CSRC, src), '-o', out]
     r = subprocess.run(cmd, capture_output=True, text=True)
     return src, r.returncode, r.stdout + r.stderr, out
 
@@ -36,6 +42,8 @@ def build(verbose=False, force=False):
     """Compile (if any source is newer than the library) and return the .so path."""
     srcs = [os.path.join(CSRC, s) for s in SOURCES] + [os.path.join(CSRC, h) for h in os.listdir(CSRC) if h.endswith(('.h', '.cuh'))]
     srcs.append(os.path.join(HERE, '..', 'include', 'igapw.h'))
+    if _extra():
+        force = True
     if not force and os.path.exists(LIB):
         newest = max(os.path.getmtime(s) for s in srcs)
         if os.path.getmtime(LIB) >= newest:

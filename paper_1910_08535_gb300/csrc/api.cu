@@ -81,11 +81,14 @@ int fail(igapw_ctx* c, int code, const std::string& msg) {
                         std::string(#x) + ": " + cudaGetErrorString(e_));                           \
     } while (0)
 
+// Device buffers are stream-ordered allocations on the context stream, so
+// creating and destroying contexts never synchronises the whole device (other
+// contexts keep running, e.g. while a request server evicts one).
 template <typename T>
 cudaError_t dalloc(igapw_ctx* c, T** p, size_t count) {
     *p = nullptr;
     if (count == 0) count = 1;
-    cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
+    cudaError_t e = cudaMallocAsync((void**)p, count * sizeof(T), c->stream);
     if (e == cudaSuccess) c->allocs.push_back(*p);
     return e;
 }
@@ -387,7 +390,7 @@ void release(igapw_ctx* c) {
         delete c->fdm;
         c->fdm = nullptr;
     }
-    for (void* p : c->allocs) cudaFree(p);
+    for (void* p : c->allocs) cudaFreeAsync(p, c->stream);
     c->allocs.clear();
 }
 

@@ -1,6 +1,7 @@
 // Shared device definitions: double-float (FP32 pair) arithmetic, per-axis
 // device descriptors, and the status word.
 #pragma once
+#include <cstdio>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -133,6 +134,23 @@ struct AxisDev {
 
 // Status bits written by kernels (read back by igapw_sync_status).
 enum : unsigned { STATUS_NONFINITE = 1u, STATUS_SINGULAR = 2u };
+
+// Debug builds (-DIGAPW_BOUNDS_CHECK): index checks that report the first
+// out-of-range accesses with printf and make the caller skip them.  Release
+// builds compile the checks away.
+#ifdef IGAPW_BOUNDS_CHECK
+static __device__ int g_igapw_nbad;
+__device__ __forceinline__ bool igapw_check_idx(const char* site, long long i, long long lim) {
+    if (i >= 0 && i < lim) return true;
+    if (atomicAdd(&g_igapw_nbad, 1) < 16)
+        printf("igapw bounds: %s index %lld limit %lld block (%d,%d) thread %d\n", site, i, lim, (int)blockIdx.x,
+               (int)blockIdx.y, (int)threadIdx.x);
+    return false;
+}
+#define IGAPW_IDX(site, i, lim) igapw_check_idx(site, (long long)(i), (long long)(lim))
+#else
+#define IGAPW_IDX(site, i, lim) true
+#endif
 
 }  // namespace igapw
 

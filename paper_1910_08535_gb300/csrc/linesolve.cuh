@@ -450,6 +450,11 @@ template <typename T, int KP, int NB>
 __device__ __forceinline__ void line_solve(T* x, const int st, const int lst, const int nb,
                                            const SolveSmem<T>& S, const int P, const int* bnd,
                                            const int k, const int n) {
+#ifdef IGAPW_BOUNDS_CHECK
+    // report only: skipping one lane would desynchronise the group's shuffles
+    (void)IGAPW_IDX("solve bnd hi", bnd[P], n + 1);
+    (void)IGAPW_IDX("solve bnd lo", bnd[k], bnd[k + 1] + 1);
+#endif
     if (P == 1) {
 #pragma unroll
         for (int b = 0; b < NB; ++b)

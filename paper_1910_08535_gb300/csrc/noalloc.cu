@@ -1,12 +1,12 @@
 // Allocation-free variant of the source right-hand side (igapw_rhs_source_noalloc).
 //
 // igapw_rhs_source sums the quadrature samples one axis at a time and keeps the
-// two intermediate tensors between the passes in device memory it allocates
-// (with cudaMalloc) on its first call for a context.  Some callers cannot let a
-// library allocate at that point: hosts that reserve all device memory up front
-// and forbid later allocations, schedulers that admit work against a fixed
-// device-memory budget, and latency-critical loops that cannot afford the
-// implicit device-wide synchronisation of cudaMalloc.  This entry point takes
+// two intermediate tensors between the passes in device memory it allocates on
+// its first call for a context (after waiting for the context stream).  Some
+// callers cannot let a library allocate at that point: hosts that reserve all
+// device memory up front and forbid later allocations, schedulers that admit
+// work against a fixed device-memory budget, and latency-critical loops that
+// cannot afford the wait.  This entry point takes
 // its intermediates from one statically sized device array instead and calls no
 // allocating routine.
 //

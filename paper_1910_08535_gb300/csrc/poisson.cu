@@ -26,6 +26,10 @@
 
 #include <cmath>
 #include <cstdio>
+#include <cstring>
+#include <list>
+#include <mutex>
+#include <unordered_map>
 #include <vector>
 
 #include "contract.cuh"
@@ -214,7 +218,7 @@ int lu_solve(Scratch& S, int64_t n, double* A, int64_t* ipiv, double* X, int64_t
     return 0;
 }
 
-int build_axis(FdmState& s, int a, const FdmAxisInput& in, Scratch& S, cublasHandle_t blas, std::string& err) {
+int build_axis(FdmAxisData& out, int a, const FdmAxisInput& in, Scratch& S, cublasHandle_t blas, std::string& err) {
     const int n = in.n, W = in.W;
     std::vector<int> fr, pos(n, -1);
     for (int i = 0; i < n; ++i)
@@ -328,27 +332,85 @@ int build_axis(FdmState& s, int a, const FdmAxisInput& in, Scratch& S, cublasHan
             Wf[(size_t)fr[k] + (size_t)fr[r] * n] = (float)X[(size_t)k + (size_t)r * m];
         }
     }
-    for (float** p : {&s.Wm[a], &s.Vm[a]}) {
-        FDM_CUDA(cudaMalloc((void**)p, (size_t)n * n * sizeof(float)));
-        s.allocs.push_back(*p);
-    }
-    FDM_CUDA(cudaMalloc((void**)&s.lam[a], (size_t)n * sizeof(float)));
-    s.allocs.push_back(s.lam[a]);
-    FDM_CUDA(S.h2d(s.Wm[a], Wf.data(), Wf.size() * 4));
-    FDM_CUDA(S.h2d(s.Vm[a], Vf.data(), Vf.size() * 4));
-    FDM_CUDA(S.h2d(s.lam[a], lf.data(), lf.size() * 4));
+    out.n = n;
+    FDM_CUDA(cudaGetDevice(&out.device));
+    FDM_CUDA(cudaMalloc((void**)&out.Wm, (size_t)n * n * sizeof(float)));
+    FDM_CUDA(cudaMalloc((void**)&out.Vm, (size_t)n * n * sizeof(float)));
+    FDM_CUDA(cudaMalloc((void**)&out.lam, (size_t)n * sizeof(float)));
+    FDM_CUDA(S.h2d(out.Wm, Wf.data(), Wf.size() * 4));
+    FDM_CUDA(S.h2d(out.Vm, Vf.data(), Vf.size() * 4));
+    FDM_CUDA(S.h2d(out.lam, lf.data(), lf.size() * 4));
     FDM_CUDA(cudaStreamSynchronize(S.ss));   // host vectors go out of scope
     return 0;
 }
 
 }  // namespace
 
+FdmAxisData::~FdmAxisData() {
+    if (Wm) cudaFree(Wm);
+    if (Vm) cudaFree(Vm);
+    if (lam) cudaFree(lam);
+}
+
+namespace {
+
+// Process-wide cache of diagonalised pencils, keyed by the device and the
+// exact bytes of the 1D tables (n, W, A, C, window starts, unknown flags).
+// It keeps the most recently used entries alive up to kCacheBytes of device
+// memory; contexts hold their own references, so an entry dropped from the
+// cache lives on until its last context is destroyed.
+constexpr size_t kCacheBytes = size_t(2) << 30;
+std::mutex g_cache_mu;
+std::list<std::pair<std::string, std::shared_ptr<FdmAxisData>>> g_lru;   // front = most recent
+std::unordered_map<std::string, decltype(g_lru)::iterator> g_index;
+size_t g_cache_bytes = 0;
+
+size_t entry_bytes(const FdmAxisData& d) { return ((size_t)2 * d.n * d.n + d.n) * sizeof(float); }
+
+std::string cache_key(int device, const FdmAxisInput& in) {
+    std::string k;
+    auto put = [&k](const void* p, size_t b) { k.append(reinterpret_cast<const char*>(p), b); };
+    put(&device, sizeof device);
+    put(&in.n, sizeof in.n);
+    put(&in.W, sizeof in.W);
+    put(in.A.data(), in.A.size() * sizeof(double));
+    put(in.C.data(), in.C.size() * sizeof(double));
+    put(in.fstart.data(), in.fstart.size() * sizeof(int));
+    put(in.is_free.data(), in.is_free.size() * sizeof(int));
+    return k;
+}
+
+std::shared_ptr<FdmAxisData> cache_get(const std::string& key) {
+    std::lock_guard<std::mutex> g(g_cache_mu);
+    auto it = g_index.find(key);
+    if (it == g_index.end()) return nullptr;
+    g_lru.splice(g_lru.begin(), g_lru, it->second);
+    return it->second->second;
+}
+
+void cache_put(const std::string& key, const std::shared_ptr<FdmAxisData>& d) {
+    std::lock_guard<std::mutex> g(g_cache_mu);
+    if (g_index.count(key)) return;
+    g_lru.emplace_front(key, d);
+    g_index[key] = g_lru.begin();
+    g_cache_bytes += entry_bytes(*d);
+    while (g_cache_bytes > kCacheBytes && g_lru.size() > 1) {
+        auto& last = g_lru.back();
+        g_cache_bytes -= entry_bytes(*last.second);
+        g_index.erase(last.first);
+        g_lru.pop_back();
+    }
+}
+
+}  // namespace
+
 void fdm_release(FdmState& s) {
-    for (void* p : s.allocs) cudaFree(p);
-    s.allocs.clear();
     if (s.blas) cublasDestroy(s.blas);
     s.blas = nullptr;
-    for (int a = 0; a < 3; ++a) s.Wm[a] = s.Vm[a] = s.lam[a] = nullptr;
+    for (int a = 0; a < 3; ++a) {
+        s.axis[a].reset();
+        s.Wm[a] = s.Vm[a] = s.lam[a] = nullptr;
+    }
 }
 
 int fdm_build(FdmState& s, int dim, const FdmAxisInput* ax, const int* const* is_free_dev, bool tensor,
@@ -360,19 +422,34 @@ int fdm_build(FdmState& s, int dim, const FdmAxisInput* ax, const int* const* is
         s.n[a] = a < dim ? ax[a].n : 1;
         s.is_free[a] = a < dim ? is_free_dev[a] : nullptr;
     }
-    FDM_CUDA(cudaStreamSynchronize(st));   // the folded tables are final
+    int device = 0;
+    FDM_CUDA(cudaGetDevice(&device));
     FDM_BLAS(cublasCreate(&s.blas));
-    Scratch S;
-    FDM_CUDA(cudaStreamCreateWithFlags(&S.ss, cudaStreamNonBlocking));
-    FDM_SOLVER(cusolverDnCreate(&S.solver));
-    FDM_SOLVER(cusolverDnCreateParams(&S.params));
-    FDM_SOLVER(cusolverDnSetStream(S.solver, S.ss));
-    FDM_BLAS(cublasSetStream(s.blas, S.ss));
+    std::unique_ptr<Scratch> S;   // solver set-up only on a cache miss
     for (int a = 0; a < dim; ++a) {
-        int rc = build_axis(s, a, ax[a], S, s.blas, err);
-        if (rc) return rc;
+        const std::string key = cache_key(device, ax[a]);
+        std::shared_ptr<FdmAxisData> d = cache_get(key);
+        if (!d) {
+            if (!S) {
+                S.reset(new Scratch());
+                FDM_CUDA(cudaStreamSynchronize(st));   // the folded tables are final
+                FDM_CUDA(cudaStreamCreateWithFlags(&S->ss, cudaStreamNonBlocking));
+                FDM_SOLVER(cusolverDnCreate(&S->solver));
+                FDM_SOLVER(cusolverDnCreateParams(&S->params));
+                FDM_SOLVER(cusolverDnSetStream(S->solver, S->ss));
+                FDM_BLAS(cublasSetStream(s.blas, S->ss));
+            }
+            d = std::make_shared<FdmAxisData>();
+            int rc = build_axis(*d, a, ax[a], *S, s.blas, err);
+            if (rc) return rc;
+            cache_put(key, d);
+        }
+        s.axis[a] = d;
+        s.Wm[a] = d->Wm;
+        s.Vm[a] = d->Vm;
+        s.lam[a] = d->lam;
     }
-    FDM_CUDA(cudaStreamSynchronize(S.ss));
+    if (S) FDM_CUDA(cudaStreamSynchronize(S->ss));
     FDM_BLAS(cublasSetStream(s.blas, st));
     if (tensor) FDM_BLAS(cublasSetMathMode(s.blas, CUBLAS_FP32_EMULATED_BF16X9_MATH));
     return 0;

@@ -2,6 +2,7 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <memory>
 #include <string>
 #include <vector>
 
@@ -18,20 +19,30 @@ struct FdmAxisInput {
     std::vector<int> fstart, is_free;
 };
 
-// Per-axis spectral data, embedded in the full index range [0, n): unknown
-// k of the axis' free set sits at index free[k]; boundary rows and columns
-// of W and V are zero and the boundary eigenvalues are 1 (never divided into
-// a non-zero value).
+// Spectral data of one 1D pencil, embedded in the full index range [0, n):
+// unknown k of the axis' free set sits at index free[k]; boundary rows and
+// columns of W and V are zero and the boundary eigenvalues are 1 (never
+// divided into a non-zero value).  Shared by every axis and context with the
+// same 1D tables (a process-wide cache, see poisson.cu); freed with the last
+// reference.
+struct FdmAxisData {
+    int device = 0, n = 0;
+    float* Wm = nullptr;    // n x n column-major, V^{-1} A_I^{-1}
+    float* Vm = nullptr;    // n x n column-major, V
+    float* lam = nullptr;   // n eigenvalues of A_I^{-1} L_I
+    ~FdmAxisData();
+};
+
 struct FdmState {
     int dim = 0;
     int n[3] = {1, 1, 1};
-    float* Wm[3] = {nullptr, nullptr, nullptr};   // n x n column-major, V^{-1} A_I^{-1}
-    float* Vm[3] = {nullptr, nullptr, nullptr};   // n x n column-major, V
-    float* lam[3] = {nullptr, nullptr, nullptr};  // n eigenvalues of A_I^{-1} L_I
+    std::shared_ptr<FdmAxisData> axis[3];
+    float* Wm[3] = {nullptr, nullptr, nullptr};
+    float* Vm[3] = {nullptr, nullptr, nullptr};
+    float* lam[3] = {nullptr, nullptr, nullptr};
     const int* is_free[3] = {nullptr, nullptr, nullptr};
     cublasHandle_t blas = nullptr;
     bool tensor = false;                           // FP32 GEMMs emulated on the bf16 tensor pipe
-    std::vector<void*> allocs;
 };
 
 // Builds the spectral data of every axis (FP64 LU and eigendecomposition on

@@ -57,7 +57,7 @@ __global__ void __launch_bounds__(256) solve_x_kernel(SolveArgs s, LineSys<T> S,
     const long long l0 = (long long)blockIdx.x * lpb;
     const int nl = (int)min((long long)lpb, nlines - l0);
     const SolveSmem<T> st = stage_tables<T, KP>(S, tabs);
-    if (threadIdx.x < 33) bnd[threadIdx.x] = S.b[threadIdx.x];
+    for (int e = threadIdx.x; e < 33; e += blockDim.x) bnd[e] = S.b[e];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int nw = blockDim.x >> 5;
     // warp per line, lane per row: coalesced, no index division
@@ -118,7 +118,7 @@ __global__ void __launch_bounds__(256) solve_strided_kernel(SolveArgs s, LineSys
     const int no = min(NO, outer - o0);
     const int pitch = NO * 32 + 1;
     const SolveSmem<T> st = stage_tables<T, KP>(S, tabs);
-    if (threadIdx.x < 33) bnd[threadIdx.x] = S.b[threadIdx.x];
+    for (int e = threadIdx.x; e < 33; e += blockDim.x) bnd[e] = S.b[e];
     const int cols = NO * 32;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int nw = blockDim.x >> 5;
@@ -157,6 +157,46 @@ __global__ void __launch_bounds__(256) solve_strided_kernel(SolveArgs s, LineSys
         const int i = idx >> lgNO, o = idx & (NO - 1);
         if (colok && o < no) store_out<T, OUT>(s, gbase + o * os + (long long)i * rs, buf[i * pitch + o * 32 + lane], bad);
     }
+    if (bad && s.status) atomicOr(s.status, STATUS_NONFINITE);
+}
+
+// Long y/z-lines (the 32-column block of solve_strided_kernel does not fit):
+// CW columns (a power of two <= 32) of one outer index per block, lane ->
+// (column lane % CW, row offset lane / CW); the tables are read from global
+// memory (all lanes of a lane group read the same row: broadcast L1 accesses).
+template <typename T, int KP, int IN, int OUT>
+__global__ void __launch_bounds__(256) solve_cols_kernel(SolveArgs s, LineSys<T> S, int nline, int CW, int lgCW,
+                                                         long long os, long long rs) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* buf = reinterpret_cast<T*>(smem_raw);
+    __shared__ int bnd[33];
+    const int nx = s.n[0];
+    const int x0 = blockIdx.x * CW;
+    const int nc = min(CW, nx - x0);
+    const int pitch = CW + 1;
+    const SolveSmem<T> st{S.L, S.U, S.dinv, S.G, S.H, S.PhiF, S.PhiB};
+    for (int e = threadIdx.x; e < 33; e += blockDim.x) bnd[e] = S.b[e];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int c = lane & (CW - 1), r0 = lane >> lgCW, rpw = 32 >> lgCW;
+    const long long gbase = (long long)blockIdx.y * os + x0 + c;
+    for (int i = warp * rpw + r0; i < nline; i += nw * rpw) {
+        if (!IGAPW_IDX("cols smem", i * pitch + c, nline * pitch)) continue;
+        if (c < nc && !IGAPW_IDX("cols g", gbase + (long long)i * rs, s.ntot)) continue;
+        buf[i * pitch + c] = c < nc ? load_in<T, IN>(s.in, gbase + (long long)i * rs) : T(0);
+    }
+    __syncthreads();
+    const int P = S.P;
+    const int groups = 32 / P;
+    const int grp = lane / P, k = lane - grp * P;
+    for (int base = warp * groups; base < CW; base += nw * groups) {
+        const int first = base + grp;
+        line_solve<T, KP, 1>(buf + min(first, CW), pitch, 1, first < CW ? 1 : 0, st, P, bnd, k, nline);
+    }
+    __syncthreads();
+    unsigned bad = 0;
+    for (int i = warp * rpw + r0; i < nline; i += nw * rpw)
+        if (c < nc && IGAPW_IDX("cols store", gbase + (long long)i * rs, s.ntot))
+            store_out<T, OUT>(s, gbase + (long long)i * rs, buf[i * pitch + c], bad);
     if (bad && s.status) atomicOr(s.status, STATUS_NONFINITE);
 }
 
@@ -201,7 +241,20 @@ static cudaError_t run_solve(const SolveArgs& s, const LineSys<T>& S, cudaStream
         while (NO > 1 && tb + (size_t)nline * (NO * 32 + 1) * sizeof(T) > 100 * 1024) NO >>= 1;
         const int warps = std::min(8, (NO * 32 + lines_per_warp - 1) / lines_per_warp);
         const size_t sm = tb + (size_t)nline * (NO * 32 + 1) * sizeof(T);
-        if ((int)sm > smem_limit()) return cudaErrorInvalidValue;
+        if ((int)sm > smem_limit()) {
+            // long lines: fewer columns per block, tables from global memory
+            int CW = 32;
+            while (CW > 1 && (size_t)nline * (CW + 1) * sizeof(T) > (size_t)smem_limit()) CW >>= 1;
+            const size_t sc = (size_t)nline * (CW + 1) * sizeof(T);
+            if (sc > (size_t)smem_limit()) return cudaErrorInvalidValue;
+            int lg = 0;
+            while ((1 << lg) < CW) ++lg;
+            auto kc = solve_cols_kernel<T, KP, IN, OUT>;
+            if (sc > 48 * 1024) cudaFuncSetAttribute(kc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sc);
+            dim3 grid((nx + CW - 1) / CW, outer);
+            kc<<<grid, 256, sc, st>>>(s, S, nline, CW, lg, os, rs);
+            return cudaGetLastError();
+        }
         auto k = solve_strided_kernel<T, KP, IN, OUT, NB>;
         if (sm > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         dim3 grid((nx + 31) / 32, (outer + NO - 1) / NO);

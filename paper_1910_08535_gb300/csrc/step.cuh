@@ -78,17 +78,51 @@ __global__ void __launch_bounds__(256) axis_step_kernel(const AxisStepArgs a) {
     const LineSys<TS>& LS = *(DFM ? (const LineSys<TS>*)&AX.ls32 : (const LineSys<TS>*)&AX.ls64);
     const int n = AX.n;
     const int nx = a.n[0], ny = a.n[1];
-    const int NL = XL ? a.lines_per_block : 32;
+    const int NL = a.lines_per_block;   // XL: lines; else columns, a power of two <= 32
 
     // ---- shared memory carve-up ------------------------------------------
-    // every segment starts on a 16-byte boundary (8-byte cp.async targets)
-    TS* tabs = reinterpret_cast<TS*>(smem_raw);
-    unsigned char* p = smem_raw + align16(table_elems<TS, KP>(n) * sizeof(TS));
-    VT* Ct = reinterpret_cast<VT*>(p);
-    VT* At = Ct + n * W;
-    p += align16((size_t)2 * n * W * sizeof(VT));
-    int* fs = reinterpret_cast<int*>(p);
-    p += align16((size_t)n * sizeof(int));
+    // every segment starts on a 16-byte boundary (8-byte cp.async targets).
+    // Long lines read the tables from global memory (every lane of a warp
+    // reads the same row: one broadcast L1 access) to leave room for lines.
+    const bool tg = a.tables_global != 0;
+    unsigned char* p = smem_raw;
+    SolveSmem<TS> S;
+    const VT* Ct;
+    const VT* At;
+    const int* fs;
+    if (tg) {
+        S = SolveSmem<TS>{LS.L, LS.U, LS.dinv, LS.G, LS.H, LS.PhiF, LS.PhiB};
+        if constexpr (DFM) {
+            Ct = reinterpret_cast<const VT*>(AX.C.df);
+            At = reinterpret_cast<const VT*>(AX.A.df);
+        } else {
+            Ct = reinterpret_cast<const VT*>(AX.C.d);
+            At = reinterpret_cast<const VT*>(AX.A.d);
+        }
+        fs = AX.fstart;
+    } else {
+        TS* tabs = reinterpret_cast<TS*>(p);
+        p += align16(table_elems<TS, KP>(n) * sizeof(TS));
+        VT* ct = reinterpret_cast<VT*>(p);
+        VT* at = ct + n * W;
+        p += align16((size_t)2 * n * W * sizeof(VT));
+        int* f = reinterpret_cast<int*>(p);
+        p += align16((size_t)n * sizeof(int));
+        S = stage_tables<TS, KP>(LS, tabs);
+        for (int e = threadIdx.x; e < n * W; e += blockDim.x) {
+            if constexpr (DFM) {
+                cp_async8(ct + e, AX.C.df + e);
+                cp_async8(at + e, AX.A.df + e);
+            } else {
+                cp_async8(ct + e, AX.C.d + e);
+                cp_async8(at + e, AX.A.d + e);
+            }
+        }
+        for (int e = threadIdx.x; e < n; e += blockDim.x) cp_async4(f + e, AX.fstart + e);
+        Ct = ct;
+        At = at;
+        fs = f;
+    }
     // lines carry W zero rows past n, so the contraction windows need no guards
     const int nr = n + W;
     const int pitch = XL ? (nr | 1) : NL + 1;
@@ -99,22 +133,16 @@ __global__ void __launch_bounds__(256) axis_step_kernel(const AxisStepArgs a) {
     VT* Ub = G + cap;                               // u during the contraction
     TS* X = reinterpret_cast<TS*>(Ub);              // FP32 pair mode: w0 ...
     TS* R = X + cap;                                //  ... and the residual / correction
-
-    const SolveSmem<TS> S = stage_tables<TS, KP>(LS, tabs);
-    for (int e = threadIdx.x; e < n * W; e += blockDim.x) {
-        if constexpr (DFM) {
-            cp_async8(Ct + e, AX.C.df + e);
-            cp_async8(At + e, AX.A.df + e);
-        } else {
-            cp_async8(Ct + e, AX.C.d + e);
-            cp_async8(At + e, AX.A.d + e);
-        }
-    }
-    for (int e = threadIdx.x; e < n; e += blockDim.x) cp_async4(fs + e, AX.fstart + e);
-    if (threadIdx.x < 33) bnd[threadIdx.x] = LS.b[threadIdx.x];
+    for (int e = threadIdx.x; e < 33; e += blockDim.x) bnd[e] = LS.b[e];
 
     // ---- which lines: global index of (line l, row i) ---------------------
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    // y/z-lines: lane -> column cl of the block's NL columns, row offset ro of
+    // the RPW rows a warp covers per pass
+    const int lgNL = XL ? 0 : __ffs(NL) - 1;
+    const int cl = XL ? 0 : (lane & (NL - 1));
+    const int ro = XL ? 0 : (lane >> lgNL);
+    const int RPW = XL ? 1 : (32 >> lgNL);
     long long l0 = 0, os = 0, rs = 0;
     int nl, x0 = 0;
     if (XL) {
@@ -139,6 +167,8 @@ __global__ void __launch_bounds__(256) axis_step_kernel(const AxisStepArgs a) {
                 for (int i = lane; i < n; i += 32) {
                     const long long g = gidx(l, i);
                     VT* d = buf + l * pitch + i;
+                    if (!IGAPW_IDX("step stage x smem", l * pitch + i, cap) || !IGAPW_IDX("step stage x g", g, a.ntot))
+                        continue;
                     if constexpr (DFM) {
                         cp_async4(&d->hi, (const float*)src + g);
                         cp_async4(&d->lo, (const float*)src + g + a.ntot);
@@ -147,10 +177,12 @@ __global__ void __launch_bounds__(256) axis_step_kernel(const AxisStepArgs a) {
                     }
                 }
         } else {
-            for (int i = warp; i < n; i += nw) {
-                VT* d = buf + i * pitch + lane;
-                if (lane < nl) {
-                    const long long g = gidx(lane, i);
+            for (int i = warp * RPW + ro; i < n; i += nw * RPW) {
+                VT* d = buf + i * pitch + cl;
+                if (!IGAPW_IDX("step stage c smem", i * pitch + cl, cap)) continue;
+                if (cl < nl) {
+                    const long long g = gidx(cl, i);
+                    if (!IGAPW_IDX("step stage c g", g, a.ntot)) continue;
                     if constexpr (DFM) {
                         cp_async4(&d->hi, (const float*)src + g);
                         cp_async4(&d->lo, (const float*)src + g + a.ntot);
@@ -170,18 +202,22 @@ __global__ void __launch_bounds__(256) axis_step_kernel(const AxisStepArgs a) {
             for (int l = warp; l < nl; l += nw)
                 for (int i = r0 + lane; i < r1; i += 32) f(l, i);
         } else {
-            for (int i = r0 + warp; i < r1; i += nw) f(lane, i);
+            for (int i = r0 + warp * RPW + ro; i < r1; i += nw * RPW) f(cl, i);
         }
     };
 
     // ---- P0: stage u ---------------------------------------------------------
     stage(Ub, a.u);
-    for_each(n, nr, [&](int l, int i) { Ub[i * st + l * lst] = VT{}; });
+    for_each(n, nr, [&](int l, int i) {
+        if (IGAPW_IDX("step pad", i * st + l * lst, cap)) Ub[i * st + l * lst] = VT{};
+    });
     cp_async_wait_all();
     __syncthreads();
 
     // ---- P1: g = C u along the line (compensated in pair mode) --------------
     for_each(0, n, [&](int l, int i) {
+        if (!IGAPW_IDX("step P1 ub", fs[i] * st + l * lst + (W - 1) * st, cap) || !IGAPW_IDX("step P1 g", i * st + l * lst, cap))
+            return;
         const VT* ub = Ub + fs[i] * st + l * lst;
         const VT* ct = Ct + i * W;
         if constexpr (DFM) {
@@ -241,6 +277,7 @@ __global__ void __launch_bounds__(256) axis_step_kernel(const AxisStepArgs a) {
         stage(Ub, (MODE == 0 || MODE == 3) ? a.u : a.acc);
         for (int base = warp * groups; base < nlines_b; base += nw * groups) {
             const int first = base + grp;
+            if (first < nlines_b && !IGAPW_IDX("step solve extent", first * lst + (n - 1) * st, cap)) continue;
             line_solve<TS, KP, 1>(reinterpret_cast<TS*>(G) + min(first, nlines_b) * lst, st, lst,
                                   first < nlines_b ? 1 : 0, S, P, bnd, k, n);
         }
@@ -261,6 +298,7 @@ __global__ void __launch_bounds__(256) axis_step_kernel(const AxisStepArgs a) {
     unsigned bad = 0;
     auto finish = [&](int l, int i) {
         const long long g = gidx(l, i);
+        if (!IGAPW_IDX("step finish smem", i * st + l * lst, cap) || !IGAPW_IDX("step finish g", g, a.ntot)) return;
         VT w;
         if constexpr (DFM) {
             float hi, lo;
@@ -289,8 +327,8 @@ __global__ void __launch_bounds__(256) axis_step_kernel(const AxisStepArgs a) {
         for (int l = warp; l < nl; l += nw)
             for (int i = lane; i < n; i += 32) finish(l, i);
     } else {
-        for (int i = warp; i < n; i += nw)
-            if (lane < nl) finish(lane, i);
+        for (int i = warp * RPW + ro; i < n; i += nw * RPW)
+            if (cl < nl) finish(cl, i);
     }
     if (bad && a.status) atomicOr(a.status, STATUS_NONFINITE);
 }
@@ -305,16 +343,32 @@ static cudaError_t run_axis_step(const AxisStepArgs& a0, cudaStream_t st) {
     int lim = 0, dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&lim, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    auto smem_for = [&](int nl) {
-        const int cap = xl ? nl * ((n + W) | 1) : (n + W) * (32 + 1);
-        return align16(table_elems<TS, KP>(n) * sizeof(TS)) + align16((size_t)2 * n * W * sizeof(VT)) +
-               align16((size_t)n * sizeof(int)) + (size_t)2 * cap * sizeof(VT);
+    // bytes of shared memory for nl lines (XL) or nl columns, with or without
+    // the tables staged
+    auto smem_for = [&](int nl, bool tg) {
+        const size_t cap = xl ? (size_t)nl * ((n + W) | 1) : (size_t)(n + W) * (nl + 1);
+        size_t b = (size_t)2 * cap * sizeof(VT);
+        if (!tg)
+            b += align16(table_elems<TS, KP>(n) * sizeof(TS)) + align16((size_t)2 * n * W * sizeof(VT)) +
+                 align16((size_t)n * sizeof(int));
+        return b;
     };
-    int NL = xl ? (int)std::min<long long>(32, nlines) : 32;
-    while (xl && NL > 1 && (int)smem_for(NL) > lim) NL = (NL + 1) / 2;
+    // Staged tables while enough lines share them (>= 8 x-lines, or all 32
+    // columns); long lines read them from global memory instead, with as many
+    // lines (a power of two for columns) as fit.
+    const int nl_max = xl ? (int)std::min<long long>(32, nlines) : 32;
+    int NL = nl_max;
+    bool tg = false;
+    while (xl && NL > 8 && smem_for(NL, false) > (size_t)lim) NL = (NL + 1) / 2;
+    if (smem_for(NL, false) > (size_t)lim) {
+        tg = true;
+        NL = nl_max;
+        while (NL > 1 && smem_for(NL, true) > (size_t)lim) NL = xl ? (NL + 1) / 2 : NL / 2;
+    }
     a.lines_per_block = NL;
-    const size_t sm = smem_for(NL);
-    if ((int)sm > lim) return cudaErrorInvalidValue;
+    a.tables_global = tg ? 1 : 0;
+    const size_t sm = smem_for(NL, tg);
+    if (sm > (size_t)lim) return cudaErrorInvalidValue;
     // modes 0 (first of several axes) and 3 (1D) run along x, modes 1 and 2 across
     constexpr bool XL = (MODE == 0 || MODE == 3);
     if (xl != XL) return cudaErrorInvalidValue;
@@ -324,7 +378,7 @@ static cudaError_t run_axis_step(const AxisStepArgs& a0, cudaStream_t st) {
         k<<<(unsigned)((nlines + NL - 1) / NL), 256, sm, st>>>(a);
     } else {
         const int outer = a.axis == 1 ? a.n[2] : a.n[1];
-        dim3 grid((a.n[0] + 31) / 32, outer);
+        dim3 grid((a.n[0] + NL - 1) / NL, outer);
         k<<<grid, 256, sm, st>>>(a);
     }
     return cudaGetLastError();

@@ -200,6 +200,7 @@ __global__ void factor_kernel(FactorArgs a) {
                 const double l = a.L[i * p + m - 1];
                 const int j = i - m;
                 if (j < b0) {
+                    if (!IGAPW_IDX("factor G", j - b0 + p, p)) continue;
                     a.G[i * p + (j - b0 + p)] += l;
                 } else {
                     for (int c = 0; c < p; ++c) a.G[i * p + c] -= l * a.G[j * p + c];
@@ -217,6 +218,7 @@ __global__ void factor_kernel(FactorArgs a) {
                 const double u = a.U[i * p + m - 1];
                 const int j = i + m;
                 if (j >= b1) {
+                    if (!IGAPW_IDX("factor H", j - b1, p)) continue;
                     a.H[i * p + (j - b1)] += u;
                 } else {
                     for (int c = 0; c < p; ++c) a.H[i * p + c] -= u * a.H[j * p + c];
@@ -233,6 +235,7 @@ __global__ void factor_kernel(FactorArgs a) {
             for (int e = 0; e < pp; ++e) { a.PhiF[(l * 32 + k) * pp + e] = 0.0; a.PhiB[(l * 32 + k) * pp + e] = 0.0; }
     for (int k = 0; k < P; ++k) {
         const int b0 = a.b[k], b1 = a.b[k + 1];
+        if (!IGAPW_IDX("factor chunk", b1 - p, n) || !IGAPW_IDX("factor chunk lo", b0, b1 - p + 1)) continue;
         for (int r = 0; r < p; ++r)
             for (int c = 0; c < p; ++c) {
                 a.PhiF[k * pp + r * p + c] = -a.G[(b1 - p + r) * p + c];

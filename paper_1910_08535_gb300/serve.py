@@ -1,34 +1,46 @@
-"""Continuous-batching request loop for explicit heat runs.
+"""Continuous-batching request loop for Poisson solves and explicit heat runs.
 
-Requests (2D or 3D explicit heat runs of different grid sizes and degrees)
-arrive over time.  The server keeps, per problem shape, a pool of contexts:
-each context owns its per-axis tables and factored 1D banded mass matrices
-(built once, resident on the device), its scratch, a device state buffer and
-its own CUDA stream.  A request that has arrived is admitted as soon as a slot
-of its shape is free (or a new one fits the device-memory budget); its work is
-enqueued on the slot's stream (host-to-device copy, the step graph,
-device-to-host copy) and runs concurrently with the other admitted requests.
-Completions are detected with CUDA events; latency = completion - arrival.
+Requests (2D/3D, different grid sizes, degrees and precisions) arrive over
+time.  The server keeps, per problem shape, a pool of slots.  A slot owns one
+library context -- its per-axis tables, factored 1D banded mass matrices or
+diagonalised 1D Poisson pencils, scratch -- plus the device tensors of one
+request, pinned host buffers and its own CUDA stream; all of it stays resident
+between requests.  An arrived request is admitted as soon as a slot of its
+shape is idle, or a new slot fits the device-memory budget (idle slots of
+other shapes are evicted to make room).  Its work is enqueued on the slot's
+stream and overlaps on the GPU with every other admitted request:
 
-All computation runs in libigapw; this module only schedules.  Poisson-solve
-requests need a multi-D Poisson solver, which is not part of the library yet,
-so the request mix is heat runs only.
+  heat     host-to-device copy of the initial coefficients, `steps` explicit
+           steps (one CUDA graph), device-to-host copy of the result;
+  poisson  the manufactured source prod_a sin(k_a pi x_a) sampled at the
+           quadrature points on the device, the source RHS, the multi-D
+           Poisson solve, device-to-host copy of the solution.
+
+Completion is detected by polling a CUDA event per slot; a request's latency
+is completion time minus arrival time.  Every arithmetic step of the method
+runs in libigapw; this module schedules, and samples the source (input
+generation) with elementwise torch operations.
 """
 import collections
 import dataclasses
-import heapq
 import time
 
 import numpy as np
 
+# grid-size ladders: log-uniform draws snap to 16 geometric rungs per range, so
+# that shapes repeat and resident slots are reused
+LADDER_2D = tuple(int(v) for v in np.unique(np.round(np.geomspace(64, 1024, 16))))
+LADDER_3D = tuple(int(v) for v in np.unique(np.round(np.geomspace(32, 160, 16))))
+
 
 @dataclasses.dataclass(frozen=True)
 class Shape:
+    kind: str            # 'heat' or 'poisson'
     dim: int
     n_elem: int
     degree: int
+    precision: str       # 'fp64' or 'fp32r'
     test: str = 'pw'
-    precision: str = 'fp32r'
 
     @property
     def nq(self):
@@ -38,76 +50,121 @@ class Shape:
     def ntot(self):
         return (self.n_elem + self.degree) ** self.dim
 
+    @property
+    def nquad(self):
+        """Upper bound on the quadrature points of the tensor grid: a PW cell
+        is split at the knots inside it, so an axis has at most 2 n_elem + p
+        pieces (Galerkin: n_elem elements) of nq points."""
+        pieces = 2 * self.n_elem + self.degree if self.test == 'pw' else self.n_elem
+        return (pieces * self.nq) ** self.dim
+
 
 @dataclasses.dataclass
 class Request:
     rid: int
-    arrival: float          # seconds after the start of the stream
+    arrival: float       # seconds after the start of the stream
     shape: Shape
-    steps: int
-    dt_h2: float
-    seed: int
+    steps: int = 20      # heat
+    dt_h2: float = 0.05  # heat: dt = dt_h2 h^2 / dim
+    k: tuple = ()        # poisson: source wave numbers per axis
 
 
-def make_stream(n_requests, rate, seed=0, frac_2d=0.7, n2d=(64, 1024), n3d=(32, 160), steps=20, dt_h2=0.05):
-    """Seeded request stream: Poisson arrivals at `rate` per second; 70% 2D with
-    n_elem log-uniform in n2d, 30% 3D log-uniform in n3d, degree uniform in {2, 3}."""
+def make_stream(n_requests, rate, seed=0, frac_2d=0.7, frac_poisson=0.5, frac_fp64=0.5, steps=20, test='pw',
+                ladder_2d=LADDER_2D, ladder_3d=LADDER_3D):
+    """Seeded mixed stream: Poisson arrivals at `rate` per second (rate None:
+    all at t = 0); 70% 2D (n log-uniform on LADDER_2D), 30% 3D (LADDER_3D);
+    degree uniform in {2, 3}; Poisson solve or `steps`-step heat run 50/50;
+    FP64 or FP32 pairs 50/50; Poisson sources with k_a uniform in 1..4."""
     rng = np.random.Generator(np.random.PCG64(seed))
-    t = np.cumsum(rng.exponential(1.0 / rate, size=n_requests))
+    if rate:
+        t = np.cumsum(rng.exponential(1.0 / rate, size=n_requests))
+    else:
+        t = np.zeros(n_requests)
     out = []
-    for k in range(n_requests):
+    for r in range(n_requests):
         two = rng.uniform() < frac_2d
-        lo, hi = n2d if two else n3d
-        ne = int(round(np.exp(rng.uniform(np.log(lo), np.log(hi)))))
+        ladder = ladder_2d if two else ladder_3d
+        ne = ladder[int(rng.integers(0, len(ladder)))]
         p = int(rng.integers(2, 4))
-        out.append(Request(k, float(t[k]), Shape(2 if two else 3, ne, p), steps, dt_h2 / (3 if not two else 2),
-                           int(rng.integers(0, 2 ** 31))))
+        kind = 'poisson' if rng.uniform() < frac_poisson else 'heat'
+        prec = 'fp64' if rng.uniform() < frac_fp64 else 'fp32r'
+        dim = 2 if two else 3
+        k = tuple(int(v) for v in rng.integers(1, 5, size=dim))
+        out.append(Request(r, float(t[r]), Shape(kind, dim, ne, p, prec, test), steps=steps, k=k))
     return out
 
 
-def initial_state(req):
-    from . import workloads
-    n = req.shape.n_elem + req.shape.degree
-    return workloads.normal_coeffs((n,) * req.shape.dim, seed=req.seed)
+def base_state(shape):
+    """Initial heat coefficients of a shape: seeded standard normal x 1e-2."""
+    n = shape.n_elem + shape.degree
+    seed = (shape.dim * 1000 + shape.n_elem) * 10 + shape.degree
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return 1e-2 * rng.standard_normal((n,) * shape.dim)
 
 
 def slot_bytes(shape):
-    """Device bytes a slot holds: state + scratch (pair or FP64: 8 B/DOF each),
-    the contexts' split-step accumulator, plus tables (small)."""
-    return 3 * 8 * shape.ntot + (1 << 20)
+    """Device bytes a slot holds (estimate): tensors and scratch at 8 bytes per
+    coefficient, the Poisson source samples and dense 1D transforms."""
+    n = shape.n_elem + shape.degree
+    b = 6 * 8 * shape.ntot + (4 << 20)
+    if shape.kind == 'poisson':
+        b += (8 if shape.precision == 'fp64' else 4) * shape.nquad + shape.dim * 2 * 4 * n * n
+    return b
 
 
 class Slot:
-    def __init__(self, shape, stream):
+    """One resident context with the device and pinned host buffers of one
+    request at a time."""
+
+    def __init__(self, shape):
         import torch
         from .igapw import Context
         self.shape = shape
-        self.stream = stream
-        with torch.cuda.stream(stream):
-            self.ctx = Context(dim=shape.dim, n_elem=shape.n_elem, degree=shape.degree, nq=shape.nq,
-                               test=shape.test, precision=shape.precision, stream=stream)
+        self.stream = torch.cuda.Stream()
+        op, bc = ('poisson', 'dirichlet0') if shape.kind == 'poisson' else ('heat', 'none')
+        self.ctx = Context(dim=shape.dim, n_elem=shape.n_elem, degree=shape.degree, nq=shape.nq, test=shape.test,
+                           precision=shape.precision, op=op, bc=bc, stream=self.stream)
+        fp64 = shape.precision == 'fp64'
+        planes = 1 if fp64 else 2
+        hdtype = torch.float64 if fp64 else torch.float32
+        with torch.cuda.stream(self.stream):
             self.u = self.ctx.empty()
-        n = self.ctx.ntot * (1 if shape.precision == 'fp64' else 2)
-        dtype = torch.float64 if shape.precision == 'fp64' else torch.float32
-        self.host_in = torch.empty(n, dtype=dtype).pin_memory()
-        self.host_out = torch.empty(n, dtype=dtype).pin_memory()
+            if shape.kind == 'poisson':
+                self.b = self.ctx.empty()
+                self.qx = [torch.from_numpy(self.ctx.quad_points(a)[0]).to('cuda', hdtype) for a in range(shape.dim)]
+                self.f = torch.empty(tuple(len(q) for q in reversed(self.qx)), dtype=hdtype, device='cuda')
+        self.host_out = torch.empty(planes * self.ctx.ntot, dtype=hdtype).pin_memory()
+        if shape.kind == 'heat':
+            u0 = base_state(shape).ravel()
+            self.host_in = torch.empty(planes * self.ctx.ntot, dtype=hdtype).pin_memory()
+            if fp64:
+                self.host_in.numpy()[:] = u0
+            else:
+                hi = u0.astype(np.float32)
+                self.host_in.numpy()[:] = np.concatenate([hi, (u0 - hi.astype(np.float64)).astype(np.float32)])
+        self.h2d_bytes = self.host_in.numel() * self.host_in.element_size() if shape.kind == 'heat' else 0
+        self.d2h_bytes = self.host_out.numel() * self.host_out.element_size()
         self.done = torch.cuda.Event()
         self.req = None
 
-    def launch(self, req, u0):
-        """Enqueue the whole request on the slot's stream (asynchronous)."""
+    def launch(self, req):
+        """Enqueue the whole request on the slot's stream (returns at once)."""
         import torch
-        arr = np.ascontiguousarray(u0, dtype=np.float64).ravel()
-        if self.shape.precision == 'fp64':
-            self.host_in.numpy()[:] = arr
-        else:
-            hi = arr.astype(np.float32)
-            lo = (arr - hi.astype(np.float64)).astype(np.float32)
-            self.host_in.numpy()[:] = np.concatenate([hi, lo])
-        dt = req.dt_h2 / req.shape.n_elem ** 2
+        sh = self.shape
         with torch.cuda.stream(self.stream):
-            self.u.view(-1).copy_(self.host_in, non_blocking=True)
-            self.ctx.step(self.u, dt, req.steps)
+            if sh.kind == 'heat':
+                self.u.view(-1).copy_(self.host_in, non_blocking=True)
+                self.ctx.step(self.u, req.dt_h2 / (sh.n_elem ** 2 * sh.dim), req.steps)
+            else:
+                scale = float(np.pi ** 2 * sum(k * k for k in req.k))
+                fac = [torch.sin((req.k[a] * np.pi) * self.qx[a]) for a in range(sh.dim)]
+                if sh.dim == 2:
+                    torch.mul(fac[1].view(-1, 1), fac[0].view(1, -1) * scale, out=self.f)
+                else:
+                    torch.mul(fac[2].view(-1, 1, 1), (fac[1].view(-1, 1) * fac[0].view(1, -1) * scale).unsqueeze(0),
+                              out=self.f)
+                self.ctx.rhs_source(self.f, out=self.b)
+                self.ctx.solve(self.b, out=self.u)
             self.host_out.copy_(self.u.view(-1), non_blocking=True)
             self.done.record(self.stream)
         self.req = req
@@ -119,55 +176,75 @@ class Slot:
         n = self.ctx.ntot
         return (a[:n].astype(np.float64) + a[n:].astype(np.float64)).reshape(self.ctx.shape)
 
+    def close(self):
+        self.ctx.close()
+
 
 class Server:
-    """Continuous-batching scheduler over per-shape slot pools."""
+    """Continuous-batching scheduler over per-shape slot pools under a
+    device-memory budget."""
 
-    def __init__(self, budget_bytes, max_inflight=64):
+    def __init__(self, budget_bytes=120 * 10 ** 9, max_inflight=32):
         self.budget = budget_bytes
         self.max_inflight = max_inflight
         self.pools = collections.defaultdict(list)   # shape -> idle slots
-        self.used_bytes = 0
+        self.used = 0
         self.inflight = []
-        self.streams = []
+        self.created = 0
+        self.evicted = 0
 
-    def _slot_for(self, shape):
-        import torch
+    def _evict_idle(self, need):
+        for sh in list(self.pools):
+            lst = self.pools[sh]
+            while lst and self.used + need > self.budget:
+                lst.pop().close()
+                self.used -= slot_bytes(sh)
+                self.evicted += 1
+
+    def acquire(self, shape):
+        """An idle slot of `shape`, a new one if the budget allows, else None."""
         if self.pools[shape]:
             return self.pools[shape].pop()
         need = slot_bytes(shape)
-        if self.used_bytes + need > self.budget:
-            # evict idle slots of other shapes to make room
-            for sh, lst in list(self.pools.items()):
-                while lst and self.used_bytes + need > self.budget:
-                    s = lst.pop()
-                    s.ctx.close()
-                    self.used_bytes -= slot_bytes(sh)
-            if self.used_bytes + need > self.budget:
+        if need > self.budget:
+            raise ValueError(f'request needs {need} bytes, above the whole budget')
+        if self.used + need > self.budget:
+            self._evict_idle(need)
+            if self.used + need > self.budget:
                 return None
-        s = Slot(shape, torch.cuda.Stream())
-        self.used_bytes += need
+        s = Slot(shape)
+        self.used += need
+        self.created += 1
         return s
 
+    def warm(self, shapes):
+        """Create (and park) one slot per shape ahead of a stream."""
+        for sh in shapes:
+            if not self.pools[sh] and self.used + slot_bytes(sh) <= self.budget:
+                self.pools[sh].append(self.acquire(sh))
+
     def run(self, requests, keep_results=False, clock=time.perf_counter):
-        """Serve `requests` (sorted by arrival); returns per-request records."""
-        pending = collections.deque(sorted(requests, key=lambda r: r.arrival))
-        records = {}
-        results = {}
+        """Serve `requests`; returns (records by rid, results by rid)."""
+        pending = collections.deque(sorted(requests, key=lambda r: (r.arrival, r.rid)))
+        records, results = {}, {}
         t0 = clock()
         while pending or self.inflight:
             now = clock() - t0
-            # admit every arrived request that fits, in arrival order
+            # admit arrived requests in order while slots and memory allow
             while pending and pending[0].arrival <= now and len(self.inflight) < self.max_inflight:
                 req = pending[0]
-                slot = self._slot_for(req.shape)
+                slot = self.acquire(req.shape)
                 if slot is None:
                     break
                 pending.popleft()
-                slot.launch(req, initial_state(req))
-                records[req.rid] = {'arrival': req.arrival, 'admit': clock() - t0, 'dim': req.shape.dim,
-                                    'n_elem': req.shape.n_elem, 'degree': req.shape.degree,
-                                    'dof': req.shape.ntot, 'steps': req.steps}
+                admit = clock() - t0
+                slot.launch(req)
+                records[req.rid] = {'arrival': req.arrival, 'admit': admit, 'kind': req.shape.kind,
+                                    'dim': req.shape.dim, 'n_elem': req.shape.n_elem,
+                                    'degree': req.shape.degree, 'precision': req.shape.precision,
+                                    'dof': req.shape.ntot, 'steps': req.steps if req.shape.kind == 'heat' else 0,
+                                    'h2d': slot.h2d_bytes, 'd2h': slot.d2h_bytes,
+                                    'bytes': slot_bytes(req.shape)}
                 self.inflight.append(slot)
             # retire finished requests
             still = []
@@ -183,23 +260,41 @@ class Server:
                 else:
                     still.append(s)
             self.inflight = still
-            if not self.inflight and pending and pending[0].arrival > clock() - t0:
-                time.sleep(min(0.001, pending[0].arrival - (clock() - t0)))
+            if not self.inflight and pending:
+                wait = pending[0].arrival - (clock() - t0)
+                if wait > 0:
+                    time.sleep(min(wait, 0.002))
         return records, results
+
+    def check(self):
+        """Raises if any context recorded an asynchronous error."""
+        for lst in self.pools.values():
+            for s in lst:
+                s.ctx.sync()
 
     def close(self):
         for lst in self.pools.values():
             for s in lst:
-                s.ctx.close()
+                s.close()
         self.pools.clear()
-        self.used_bytes = 0
+        self.used = 0
 
 
 def summarize(records):
     lat = np.array([r['latency'] for r in records.values()])
     t_end = max(r['done'] for r in records.values())
-    dof_upd = sum(r['dof'] * r['steps'] for r in records.values())
-    return {'requests': len(records), 'p50_ms': float(np.percentile(lat, 50) * 1e3),
-            'p99_ms': float(np.percentile(lat, 99) * 1e3), 'mean_ms': float(lat.mean() * 1e3),
-            'throughput_req_s': len(records) / t_end, 'dof_updates_per_s': dof_upd / t_end,
-            'makespan_s': t_end}
+    t_start = min(r['arrival'] for r in records.values())
+    span = max(t_end - t_start, 1e-9)
+    heat_upd = sum(r['dof'] * r['steps'] for r in records.values())
+    out = {'requests': len(records), 'p50_ms': float(np.percentile(lat, 50) * 1e3),
+           'p99_ms': float(np.percentile(lat, 99) * 1e3), 'mean_ms': float(lat.mean() * 1e3),
+           'max_ms': float(lat.max() * 1e3), 'throughput_req_s': len(records) / span,
+           'heat_dof_updates_per_s': heat_upd / span, 'makespan_s': span,
+           'h2d_bytes': int(sum(r['h2d'] for r in records.values())),
+           'd2h_bytes': int(sum(r['d2h'] for r in records.values()))}
+    for kind in ('heat', 'poisson'):
+        l = np.array([r['latency'] for r in records.values() if r['kind'] == kind])
+        if len(l):
+            out[f'{kind}_p50_ms'] = float(np.percentile(l, 50) * 1e3)
+            out[f'{kind}_p99_ms'] = float(np.percentile(l, 99) * 1e3)
+    return out
