@@ -37,6 +37,7 @@ def parse():
     ap.add_argument('--warmup', type=int, default=3)
     ap.add_argument('--impl', default='native', choices=['native', 'reference'])
     ap.add_argument('--residual', default='df', choices=['fp64', 'df'])
+    ap.add_argument('--no-serve', action='store_true', help='skip the request-stream measurement')
     return ap.parse_args()
 
 
@@ -269,6 +270,95 @@ def measure_source_table1(stream, flush, hbm_peak, reps=5):
     return res
 
 
+def measure_poisson(stream, flush, reps=10):
+    """Row a7 (multi-D Poisson, Sec. 4.3 problem): 2D, 1024^2 elements, cubic
+    PW tests, solve K u = b by fast diagonalisation (FP32 GEMM transforms per
+    axis) inside iterative refinement; FP32 pairs (1 correction) and FP64 (3
+    corrections), plain FP32 GEMMs and BF16x9 tensor-pipe emulation.  The
+    GEMM work of one transform application is 2 x sum_a 2 n_a N flops (W's
+    then V's; N coefficients)."""
+    import numpy as np
+    import torch
+    from paper_1910_08535_gb300 import igapw, workloads
+    from paper_1910_08535_gb300.igapw import Context
+    ne, p = 1024, 3
+    res = {}
+    for prec in ('fp32r', 'fp64'):
+        for tag, flags in (('fp32_gemm', 0), ('bf16x9', igapw.IGAPW_FLAG_FDM_BF16X9)):
+            with torch.cuda.stream(stream):
+                t_create = time.perf_counter()
+                c = Context(dim=2, n_elem=ne, degree=p, nq=p + 1, test='pw', precision=prec, op='poisson',
+                            bc='dirichlet0', flags=flags, stream=stream)
+                t_create = time.perf_counter() - t_create
+                pts = [c.quad_points(a)[0] for a in range(2)]
+                f = workloads.sine_product_source(pts, (1, 2))
+                fd = torch.from_numpy(f.astype(np.float64 if prec == 'fp64' else np.float32)).cuda()
+                b = c.rhs_source(fd)
+                u = c.empty()
+                t = _time_events(stream, lambda: c.solve(b, out=u), reps, flush)
+                c.sync()
+            applications = 2 if prec == 'fp32r' else 4
+            flops = applications * 2 * sum(2 * c.n[a] * c.ntot for a in range(2))
+            res[f'{prec}_{tag}'] = {'us': t * 1e6, 'dof_per_s': c.ntot / t, 'gemm_tflops': flops / t / 1e12,
+                                    'fdm_applications': applications, 'create_s': t_create,
+                                    'solution': c.to_numpy(u), 'rhs': c.to_numpy(b)}
+            c.close()
+    return res
+
+
+def measure_serving(requests=2000, seed=6, budget=120 * 10 ** 9):
+    """Mixed request stream (Poisson solves and 20-step heat runs, 70% 2D
+    64^2..1024^2 / 30% 3D 32^3..160^3, p in {2,3}, FP64 / FP32 pairs) through
+    the continuous-batching server: slots for every shape created first
+    (resident tables, factors and pencils), capacity from a closed-loop run of
+    300 requests, then `requests` Poisson arrivals at 80% of that capacity."""
+    import torch
+    from paper_1910_08535_gb300 import serve
+    srv = serve.Server(budget_bytes=budget)
+    stream = serve.make_stream(requests, rate=1.0, seed=seed)
+    probe = serve.make_stream(300, rate=None, seed=seed + 1)
+    t0 = time.perf_counter()
+    srv.warm(sorted({r.shape for r in stream + probe}, key=str))
+    torch.cuda.synchronize()
+    t_warm = time.perf_counter() - t0
+    recs, _ = srv.run(probe)
+    srv.check()
+    cap = serve.summarize(recs)['throughput_req_s']
+    rate = 0.8 * cap
+    stream = serve.make_stream(requests, rate=rate, seed=seed)
+    recs, _ = srv.run(stream)
+    srv.check()
+    out = serve.summarize(recs)
+    out.update({'capacity_req_s': cap, 'arrival_rate_req_s': rate, 'budget_bytes': budget,
+                'resident_bytes': srv.used, 'slots': sum(len(v) for v in srv.pools.values()),
+                'warm_s': t_warm, 'evicted': srv.evicted,
+                'mix': '70% 2D (64..1024)^2 / 30% 3D (32..160)^3 on 16-rung geometric ladders, p in {2,3}, '
+                       'Poisson solve / 20-step heat 50/50, FP64 / FP32 pairs 50/50, PW tests'})
+    srv.close()
+    return out
+
+
+def cpu_baseline_poisson(res):
+    """Oracle side of row a7: the backward error of the GPU solutions at full
+    size (the oracle applies K by per-axis contractions; a sparse direct
+    solve at 1M unknowns is out of reach here) and the oracle's sparse direct
+    solve timed on a 256^2 sample."""
+    import numpy as np
+    from oracle import poisson_nd, systems
+    ne, p = 1024, 3
+    axes = [systems.Axis(ne, p, p + 1, 'pw', 'dirichlet0') for _ in range(2)]
+    out = {}
+    for k, v in res.items():
+        out[k] = {kk: vv for kk, vv in v.items() if kk not in ('solution', 'rhs')}
+        out[k]['backward_error_vs_oracle'] = poisson_nd.backward_error(axes, v['solution'], v['rhs'])
+    small = [systems.Axis(256, p, p + 1, 'pw', 'dirichlet0') for _ in range(2)]
+    b = np.random.default_rng(0).standard_normal((259, 259))
+    t0 = time.perf_counter()
+    poisson_nd.solve(small, b, sparse=True)
+    out['oracle_sparse_direct_256x256_s'] = time.perf_counter() - t0
+    return out
+
+
 def run_native(args, rank, world):
     import numpy as np
     import torch
@@ -376,6 +466,10 @@ def run_native(args, rank, world):
 
     rows = measure_rows(c, u, dt, stream, flush, hbm_peak)
     rows['a4_source_table1'] = measure_source_table1(stream, flush, hbm_peak)
+    poisson = measure_poisson(stream, flush)
+    rows['a7_poisson_2d_1024'] = cpu_baseline_poisson(poisson)
+    # the request server is a one-GPU process: measured at N = 1
+    serving = measure_serving() if (world == 1 and not args.no_serve) else None
 
     cpu = None
     if rank == 0 and world == 1:
@@ -392,6 +486,7 @@ def run_native(args, rank, world):
                        'l2': 'flushed (512 MB write) before every timed step', 'residual': args.residual},
             'galerkin': {'value': value_g, 'unit': 'DOF-updates/s', 'pw_over_galerkin': value / value_g},
             'roofline': roof, 'hbm_view': hbm_view, 'clocks': clocks, 'e2e': e2e, 'rows': rows,
+            'serving': serving,
             'gpu_launches': launches_per_time_step * nsteps * args.steps,
             'cpu_baseline': cpu}
     if rank == 0:

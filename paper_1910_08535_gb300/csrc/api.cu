@@ -587,12 +587,10 @@ int igapw_solve(igapw_ctx* c, const void* r_dev, void* u_dev) {
     if (!r_dev || !u_dev) return fail(c, IGAPW_ERR_ARG, "NULL tensor");
     if (c->fdm) {
         if (r_dev == u_dev) return fail(c, IGAPW_ERR_ARG, "the multi-D Poisson solve needs distinct r and u");
-        float* t0 = (float*)c->r;                  // 2 ntot floats in both precisions
-        float* t1 = t0 + c->ntot;
         float* rho = fp64(c) ? (float*)c->w : c->rho;
         std::string err;
-        const int rc = fdm_solve(*c->fdm, contract_args(c), r_dev, u_dev, fp64(c), kPoissonRefineF64, t0, t1, rho,
-                                 c->u0, (c->d.flags & IGAPW_FLAG_FP64_RESIDUAL) != 0, c->stream, err);
+        const int rc = fdm_solve(*c->fdm, contract_args(c), r_dev, u_dev, fp64(c), kPoissonRefineF64, rho, c->u0,
+                                 (c->d.flags & IGAPW_FLAG_FP64_RESIDUAL) != 0, c->stream, err);
         if (rc) return fail(c, rc, "Poisson solve: " + err);
         return IGAPW_OK;
     }

@@ -113,8 +113,6 @@ struct AxisStepArgs {
     int W;
     int lines_per_block;    // lines staged per block: x-lines, or columns (a power of
                             // two <= 32) of y/z-lines (set by the launcher)
-    int tables_global;      // 1: read the 1D tables from global memory (L1/L2) instead of
-                            // staging them in shared memory (long lines; set by the launcher)
     long long ntot;
     AxisDev ax;
     const void* u;

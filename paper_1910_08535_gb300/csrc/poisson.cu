@@ -68,20 +68,26 @@ cudaError_t launch_poisson_contract(const ContractArgs& a, int mode, int cmp, in
 }
 
 // ---- elementwise kernels ------------------------------------------------------
-// Grid: (ceil(n_x / 256), n_y, n_z); one thread per coefficient.
+// Coefficient tensors are (n_z, n_y, n_x); the spectral-domain buffers of the
+// transforms are (n_z, n_y, px) with the x pitch px padded to a multiple of 8
+// (32-byte aligned GEMM leading dimensions), zero in the padding columns.
+// Grid: (ceil(px / 256), n_y, n_z); one thread per (padded) coefficient.
 struct Grid3 {
     int n[3];
+    int px;
     long long ntot;
     const int* is_free[3];   // NULL beyond the problem's dimension
-    const float* lam[3];     // NULL beyond the problem's dimension
+    const float* lam[3];     // padded eigenvalues; NULL beyond the problem's dimension
 };
 
-__device__ __forceinline__ bool grid_index(const Grid3& g, int& x, int& y, int& z, long long& i) {
+__device__ __forceinline__ bool grid_index(const Grid3& g, int& x, int& y, int& z, long long& i, long long& ip) {
     x = blockIdx.x * blockDim.x + threadIdx.x;
     y = blockIdx.y;
     z = blockIdx.z;
-    if (x >= g.n[0]) return false;
-    i = ((long long)z * g.n[1] + y) * g.n[0] + x;
+    if (x >= g.px) return false;
+    const long long row = (long long)z * g.n[1] + y;
+    i = row * g.n[0] + x;
+    ip = row * g.px + x;
     return true;
 }
 
@@ -92,50 +98,64 @@ __device__ __forceinline__ bool free_at(const Grid3& g, int x, int y, int z) {
     return f;
 }
 
-// t /= lx + ly + lz  (spectral domain; boundary entries are zero)
+// t = r in the padded layout (FP32 input), zero padding
+__global__ void fdm_pack_kernel(Grid3 g, const float* r, float* t) {
+    int x, y, z;
+    long long i, ip;
+    if (!grid_index(g, x, y, z, i, ip)) return;
+    t[ip] = x < g.n[0] ? r[i] : 0.f;
+}
+
+// rho = (float) b and t = rho in the padded layout (FP64 input)
+__global__ void fdm_pack_f64_kernel(Grid3 g, const double* b, float* rho, float* t) {
+    int x, y, z;
+    long long i, ip;
+    if (!grid_index(g, x, y, z, i, ip)) return;
+    float v = 0.f;
+    if (x < g.n[0]) {
+        v = (float)b[i];
+        rho[i] = v;
+    }
+    t[ip] = v;
+}
+
+// t /= lx + ly + lz  (spectral domain; boundary and padding entries are zero)
 __global__ void fdm_diag_kernel(Grid3 g, float* t) {
     int x, y, z;
-    long long i;
-    if (!grid_index(g, x, y, z, i)) return;
+    long long i, ip;
+    if (!grid_index(g, x, y, z, i, ip)) return;
     float s = g.lam[0][x];
     if (g.lam[1]) s += g.lam[1][y];
     if (g.lam[2]) s += g.lam[2][z];
-    t[i] = t[i] / s;
+    t[ip] = t[ip] / s;
 }
 
 // u0 = P r: the transformed value off the boundary, r itself on it
 __global__ void fdm_first_kernel(Grid3 g, const float* t, const float* r, float* u0) {
     int x, y, z;
-    long long i;
-    if (!grid_index(g, x, y, z, i)) return;
-    u0[i] = free_at(g, x, y, z) ? t[i] : r[i];
+    long long i, ip;
+    if (!grid_index(g, x, y, z, i, ip) || x >= g.n[0]) return;
+    u0[i] = free_at(g, x, y, z) ? t[ip] : r[i];
 }
 
 // pair output (hi, lo) = u0 + P rho, rounded to nearest as a double-float
 __global__ void fdm_final_pair_kernel(Grid3 g, const float* u0, const float* t, const float* rho, float* out) {
     int x, y, z;
-    long long i;
-    if (!grid_index(g, x, y, z, i)) return;
-    const float d = free_at(g, x, y, z) ? t[i] : rho[i];
+    long long i, ip;
+    if (!grid_index(g, x, y, z, i, ip) || x >= g.n[0]) return;
+    const float d = free_at(g, x, y, z) ? t[ip] : rho[i];
     float s, e;
     two_sum(u0[i], d, s, e);
     out[i] = s;
     out[i + g.ntot] = e;
 }
 
-__global__ void fdm_to_f32_kernel(Grid3 g, const double* b, float* r) {
-    int x, y, z;
-    long long i;
-    if (!grid_index(g, x, y, z, i)) return;
-    r[i] = (float)b[i];
-}
-
 // u = (first ? 0 : u) + P rho in FP64
 __global__ void fdm_update_f64_kernel(Grid3 g, const float* t, const float* rho, double* u, int first) {
     int x, y, z;
-    long long i;
-    if (!grid_index(g, x, y, z, i)) return;
-    const double d = (double)(free_at(g, x, y, z) ? t[i] : rho[i]);
+    long long i, ip;
+    if (!grid_index(g, x, y, z, i, ip) || x >= g.n[0]) return;
+    const double d = (double)(free_at(g, x, y, z) ? t[ip] : rho[i]);
     u[i] = first ? d : u[i] + d;
 }
 
@@ -166,6 +186,8 @@ namespace {
             return -4;                                                                      \
         }                                                                                   \
     } while (0)
+
+int pad8(int n) { return (n + 7) & ~7; }
 
 // Scoped device buffers, solver handle and private stream of one fdm_build
 // call.  Buffers are stream-ordered (cudaMallocAsync / cudaFreeAsync) so that
@@ -323,20 +345,22 @@ int build_axis(FdmAxisData& out, int a, const FdmAxisInput& in, Scratch& S, cubl
             return -4;
         }
     }
-    // embed in the full index range as FP32
-    std::vector<float> Wf((size_t)n * n, 0.f), Vf((size_t)n * n, 0.f), lf(n, 1.f);
+    // embed in the full index range as FP32, padded to np = a multiple of 8
+    const int np = pad8(n);
+    std::vector<float> Wf((size_t)np * np, 0.f), Vf((size_t)np * np, 0.f), lf(np, 1.f);
     for (int64_t k = 0; k < m; ++k) {
         lf[fr[k]] = (float)lam_c[k].x;
         for (int64_t r = 0; r < m; ++r) {
-            Vf[(size_t)fr[r] + (size_t)fr[k] * n] = (float)V[(size_t)r + (size_t)k * m];
-            Wf[(size_t)fr[k] + (size_t)fr[r] * n] = (float)X[(size_t)k + (size_t)r * m];
+            Vf[(size_t)fr[r] + (size_t)fr[k] * np] = (float)V[(size_t)r + (size_t)k * m];
+            Wf[(size_t)fr[k] + (size_t)fr[r] * np] = (float)X[(size_t)k + (size_t)r * m];
         }
     }
     out.n = n;
+    out.np = np;
     FDM_CUDA(cudaGetDevice(&out.device));
-    FDM_CUDA(cudaMalloc((void**)&out.Wm, (size_t)n * n * sizeof(float)));
-    FDM_CUDA(cudaMalloc((void**)&out.Vm, (size_t)n * n * sizeof(float)));
-    FDM_CUDA(cudaMalloc((void**)&out.lam, (size_t)n * sizeof(float)));
+    FDM_CUDA(cudaMalloc((void**)&out.Wm, (size_t)np * np * sizeof(float)));
+    FDM_CUDA(cudaMalloc((void**)&out.Vm, (size_t)np * np * sizeof(float)));
+    FDM_CUDA(cudaMalloc((void**)&out.lam, (size_t)np * sizeof(float)));
     FDM_CUDA(S.h2d(out.Wm, Wf.data(), Wf.size() * 4));
     FDM_CUDA(S.h2d(out.Vm, Vf.data(), Vf.size() * 4));
     FDM_CUDA(S.h2d(out.lam, lf.data(), lf.size() * 4));
@@ -365,7 +389,7 @@ std::list<std::pair<std::string, std::shared_ptr<FdmAxisData>>> g_lru;   // fron
 std::unordered_map<std::string, decltype(g_lru)::iterator> g_index;
 size_t g_cache_bytes = 0;
 
-size_t entry_bytes(const FdmAxisData& d) { return ((size_t)2 * d.n * d.n + d.n) * sizeof(float); }
+size_t entry_bytes(const FdmAxisData& d) { return ((size_t)2 * d.np * d.np + d.np) * sizeof(float); }
 
 std::string cache_key(int device, const FdmAxisInput& in) {
     std::string k;
@@ -405,6 +429,9 @@ void cache_put(const std::string& key, const std::shared_ptr<FdmAxisData>& d) {
 }  // namespace
 
 void fdm_release(FdmState& s) {
+    for (int k = 0; k < 2; ++k)
+        if (s.t[k]) cudaFreeAsync(s.t[k], s.stream);
+    s.t[0] = s.t[1] = nullptr;
     if (s.blas) cublasDestroy(s.blas);
     s.blas = nullptr;
     for (int a = 0; a < 3; ++a) {
@@ -418,10 +445,14 @@ int fdm_build(FdmState& s, int dim, const FdmAxisInput* ax, const int* const* is
     fdm_release(s);
     s.dim = dim;
     s.tensor = tensor;
+    s.stream = st;
     for (int a = 0; a < 3; ++a) {
         s.n[a] = a < dim ? ax[a].n : 1;
         s.is_free[a] = a < dim ? is_free_dev[a] : nullptr;
     }
+    s.px = pad8(s.n[0]);
+    const size_t tbytes = (size_t)s.px * s.n[1] * s.n[2] * sizeof(float);
+    for (int k = 0; k < 2; ++k) FDM_CUDA(cudaMallocAsync((void**)&s.t[k], tbytes, st));
     int device = 0;
     FDM_CUDA(cudaGetDevice(&device));
     FDM_BLAS(cublasCreate(&s.blas));
@@ -451,28 +482,32 @@ int fdm_build(FdmState& s, int dim, const FdmAxisInput* ax, const int* const* is
     }
     if (S) FDM_CUDA(cudaStreamSynchronize(S->ss));
     FDM_BLAS(cublasSetStream(s.blas, st));
-    if (tensor) FDM_BLAS(cublasSetMathMode(s.blas, CUBLAS_FP32_EMULATED_BF16X9_MATH));
+    if (tensor) {
+        FDM_BLAS(cublasSetMathMode(s.blas, CUBLAS_FP32_EMULATED_BF16X9_MATH));
+        FDM_BLAS(cublasSetEmulationStrategy(s.blas, CUBLAS_EMULATION_STRATEGY_EAGER));
+    }
     return 0;
 }
 
 // ---- solve ---------------------------------------------------------------------
 namespace {
 
-// out = M applied along axis a of the (n_z, n_y, n_x) tensor `in`
+// out = M applied along axis a of the padded spectral tensor `in` (n_z, n_y, px)
 int gemm_axis(FdmState& s, int a, const float* M, const float* in, float* out, std::string& err) {
-    const int nx = s.n[0], ny = s.n[1], nz = s.n[2];
+    const int px = s.px, ny = s.n[1], nz = s.n[2];
+    const int ld = s.axis[a]->np;   // padded leading dimension of M
     const float one = 1.f, zero = 0.f;
     const cublasComputeType_t ct = s.tensor ? CUBLAS_COMPUTE_32F_EMULATED_16BFX9 : CUBLAS_COMPUTE_32F;
     if (a == 0) {
-        FDM_BLAS(cublasGemmEx(s.blas, CUBLAS_OP_N, CUBLAS_OP_N, nx, ny * nz, nx, &one, M, CUDA_R_32F, nx, in,
-                              CUDA_R_32F, nx, &zero, out, CUDA_R_32F, nx, ct, CUBLAS_GEMM_DEFAULT));
+        FDM_BLAS(cublasGemmEx(s.blas, CUBLAS_OP_N, CUBLAS_OP_N, px, ny * nz, px, &one, M, CUDA_R_32F, ld, in,
+                              CUDA_R_32F, px, &zero, out, CUDA_R_32F, px, ct, CUBLAS_GEMM_DEFAULT));
     } else if (a == 1) {
-        FDM_BLAS(cublasGemmStridedBatchedEx(s.blas, CUBLAS_OP_N, CUBLAS_OP_T, nx, ny, ny, &one, in, CUDA_R_32F, nx,
-                                            (long long)nx * ny, M, CUDA_R_32F, ny, 0, &zero, out, CUDA_R_32F, nx,
-                                            (long long)nx * ny, nz, ct, CUBLAS_GEMM_DEFAULT));
+        FDM_BLAS(cublasGemmStridedBatchedEx(s.blas, CUBLAS_OP_N, CUBLAS_OP_T, px, ny, ny, &one, in, CUDA_R_32F, px,
+                                            (long long)px * ny, M, CUDA_R_32F, ld, 0, &zero, out, CUDA_R_32F, px,
+                                            (long long)px * ny, nz, ct, CUBLAS_GEMM_DEFAULT));
     } else {
-        FDM_BLAS(cublasGemmEx(s.blas, CUBLAS_OP_N, CUBLAS_OP_T, nx * ny, nz, nz, &one, in, CUDA_R_32F, nx * ny, M,
-                              CUDA_R_32F, nz, &zero, out, CUDA_R_32F, nx * ny, ct, CUBLAS_GEMM_DEFAULT));
+        FDM_BLAS(cublasGemmEx(s.blas, CUBLAS_OP_N, CUBLAS_OP_T, px * ny, nz, nz, &one, in, CUDA_R_32F, px * ny, M,
+                              CUDA_R_32F, ld, &zero, out, CUDA_R_32F, px * ny, ct, CUBLAS_GEMM_DEFAULT));
     }
     return 0;
 }
@@ -484,46 +519,46 @@ Grid3 grid_of(const FdmState& s, long long ntot) {
         g.is_free[a] = s.is_free[a];
         g.lam[a] = a < s.dim ? s.lam[a] : nullptr;
     }
+    g.px = s.px;
     g.ntot = ntot;
     return g;
 }
 
-dim3 grid_dims(const Grid3& g) { return dim3((g.n[0] + 255) / 256, g.n[1], g.n[2]); }
+dim3 grid_dims(const Grid3& g) { return dim3((g.px + 255) / 256, g.n[1], g.n[2]); }
 
-// t1 = P-transform of r off the boundary (zero on it): W's, 1/(sum lambda), V's
-int apply_fdm(FdmState& s, const Grid3& g, const float* r, float* t0, float* t1, cudaStream_t st,
-              std::string& err) {
-    const float* cur = r;
-    int step = 0;
-    for (int a = 0; a < s.dim; ++a, ++step) {
-        float* out = (step % 2 == 0) ? t0 : t1;
-        int rc = gemm_axis(s, a, s.Wm[a], cur, out, err);
+// Transforms the padded tensor in s.t[0] in place (result in s.t[0]): W's,
+// 1/(sum lambda), V's -- 2 dim GEMMs ping-ponging between s.t[0] and s.t[1].
+int apply_fdm(FdmState& s, const Grid3& g, cudaStream_t st, std::string& err) {
+    float* buf[2] = {s.t[0], s.t[1]};
+    int cur = 0;
+    for (int a = 0; a < s.dim; ++a, cur ^= 1) {
+        int rc = gemm_axis(s, a, s.Wm[a], buf[cur], buf[cur ^ 1], err);
         if (rc) return rc;
-        cur = out;
     }
-    fdm_diag_kernel<<<grid_dims(g), 256, 0, st>>>(g, const_cast<float*>(cur));
+    fdm_diag_kernel<<<grid_dims(g), 256, 0, st>>>(g, buf[cur]);
     FDM_CUDA(cudaGetLastError());
-    for (int a = 0; a < s.dim; ++a, ++step) {
-        float* out = (step % 2 == 0) ? t0 : t1;
-        int rc = gemm_axis(s, a, s.Vm[a], cur, out, err);
+    for (int a = 0; a < s.dim; ++a, cur ^= 1) {
+        int rc = gemm_axis(s, a, s.Vm[a], buf[cur], buf[cur ^ 1], err);
         if (rc) return rc;
-        cur = out;
     }
-    return 0;   // 2 dim transforms: the last one wrote t1
+    return 0;
 }
 
 }  // namespace
 
-int fdm_solve(FdmState& s, const ContractArgs& ca, const void* b, void* u, bool fp64, int iters, float* t0,
-              float* t1, float* rho, float* u0, bool pair_fp64_residual, cudaStream_t st, std::string& err) {
+int fdm_solve(FdmState& s, const ContractArgs& ca, const void* b, void* u, bool fp64, int iters, float* rho,
+              float* u0, bool pair_fp64_residual, cudaStream_t st, std::string& err) {
     FDM_BLAS(cublasSetStream(s.blas, st));
     const Grid3 g = grid_of(s, ca.ntot);
     const dim3 gd = grid_dims(g);
+    const float* t = s.t[0];
     if (!fp64) {
         const float* bhi = (const float*)b;
-        int rc = apply_fdm(s, g, bhi, t0, t1, st, err);
+        fdm_pack_kernel<<<gd, 256, 0, st>>>(g, bhi, s.t[0]);
+        FDM_CUDA(cudaGetLastError());
+        int rc = apply_fdm(s, g, st, err);
         if (rc) return rc;
-        fdm_first_kernel<<<gd, 256, 0, st>>>(g, t1, bhi, u0);
+        fdm_first_kernel<<<gd, 256, 0, st>>>(g, t, bhi, u0);
         FDM_CUDA(cudaGetLastError());
         ContractArgs a = ca;
         a.u = u0;
@@ -532,18 +567,20 @@ int fdm_solve(FdmState& s, const ContractArgs& ca, const void* b, void* u, bool 
         a.alpha = 0.0;
         a.beta = -1.0;
         FDM_CUDA(launch_poisson_contract(a, MODE_PRES, pair_fp64_residual ? FMT_F64 : FMT_PAIR, FMT_PAIR, st));
-        rc = apply_fdm(s, g, rho, t0, t1, st, err);
+        fdm_pack_kernel<<<gd, 256, 0, st>>>(g, rho, s.t[0]);
+        FDM_CUDA(cudaGetLastError());
+        rc = apply_fdm(s, g, st, err);
         if (rc) return rc;
-        fdm_final_pair_kernel<<<gd, 256, 0, st>>>(g, u0, t1, rho, (float*)u);
+        fdm_final_pair_kernel<<<gd, 256, 0, st>>>(g, u0, t, rho, (float*)u);
         FDM_CUDA(cudaGetLastError());
         return 0;
     }
-    fdm_to_f32_kernel<<<gd, 256, 0, st>>>(g, (const double*)b, rho);
+    fdm_pack_f64_kernel<<<gd, 256, 0, st>>>(g, (const double*)b, rho, s.t[0]);
     FDM_CUDA(cudaGetLastError());
     for (int it = 0; it <= iters; ++it) {
-        int rc = apply_fdm(s, g, rho, t0, t1, st, err);
+        int rc = apply_fdm(s, g, st, err);
         if (rc) return rc;
-        fdm_update_f64_kernel<<<gd, 256, 0, st>>>(g, t1, rho, (double*)u, it == 0);
+        fdm_update_f64_kernel<<<gd, 256, 0, st>>>(g, t, rho, (double*)u, it == 0);
         FDM_CUDA(cudaGetLastError());
         if (it == iters) break;
         ContractArgs a = ca;
@@ -553,6 +590,8 @@ int fdm_solve(FdmState& s, const ContractArgs& ca, const void* b, void* u, bool 
         a.alpha = 0.0;
         a.beta = -1.0;
         FDM_CUDA(launch_poisson_contract(a, MODE_PRES, FMT_F64, FMT_F64, st));
+        fdm_pack_kernel<<<gd, 256, 0, st>>>(g, rho, s.t[0]);
+        FDM_CUDA(cudaGetLastError());
     }
     return 0;
 }

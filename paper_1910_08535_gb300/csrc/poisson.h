@@ -27,9 +27,10 @@ struct FdmAxisInput {
 // reference.
 struct FdmAxisData {
     int device = 0, n = 0;
-    float* Wm = nullptr;    // n x n column-major, V^{-1} A_I^{-1}
-    float* Vm = nullptr;    // n x n column-major, V
-    float* lam = nullptr;   // n eigenvalues of A_I^{-1} L_I
+    int np = 0;             // n padded to a multiple of 8 (leading dimension)
+    float* Wm = nullptr;    // np x np column-major, V^{-1} A_I^{-1} (zero padding)
+    float* Vm = nullptr;    // np x np column-major, V (zero padding)
+    float* lam = nullptr;   // np eigenvalues of A_I^{-1} L_I (1 on boundary and padding)
     ~FdmAxisData();
 };
 
@@ -41,6 +42,9 @@ struct FdmState {
     float* Vm[3] = {nullptr, nullptr, nullptr};
     float* lam[3] = {nullptr, nullptr, nullptr};
     const int* is_free[3] = {nullptr, nullptr, nullptr};
+    int px = 1;                                    // padded x pitch of the spectral buffers
+    float* t[2] = {nullptr, nullptr};              // spectral buffers, (n_z, n_y, px) floats each
+    cudaStream_t stream = nullptr;                 // stream of the buffers' allocation
     cublasHandle_t blas = nullptr;
     bool tensor = false;                           // FP32 GEMMs emulated on the bf16 tensor pipe
 };
@@ -51,11 +55,12 @@ int fdm_build(FdmState& s, int dim, const FdmAxisInput* ax, const int* const* is
               cudaStream_t st, std::string& err);
 void fdm_release(FdmState& s);
 
-// Poisson solve K u = b.  Scratch: t0, t1, rho (ntot floats each) and, for
-// pair tensors, u0 (ntot floats).  b and u are pair tensors (fp64 == false)
-// or double tensors (fp64 == true; `iters` refinement steps).
-int fdm_solve(FdmState& s, const ContractArgs& ca, const void* b, void* u, bool fp64, int iters, float* t0,
-              float* t1, float* rho, float* u0, bool pair_fp64_residual, cudaStream_t st, std::string& err);
+// Poisson solve K u = b.  Scratch: rho (ntot floats) and, for pair tensors,
+// u0 (ntot floats); the spectral buffers are the state's own.  b and u are
+// pair tensors (fp64 == false) or double tensors (fp64 == true; `iters`
+// refinement steps).
+int fdm_solve(FdmState& s, const ContractArgs& ca, const void* b, void* u, bool fp64, int iters, float* rho,
+              float* u0, bool pair_fp64_residual, cudaStream_t st, std::string& err);
 
 // r = K u (MODE_PK) or rho = r - K u (MODE_PRES) through the contraction kernel.
 cudaError_t launch_poisson_contract(const ContractArgs& a, int mode, int cmp, int io, cudaStream_t st);

@@ -68,7 +68,7 @@ __device__ __forceinline__ void st_state(void* p, long long g, long long, double
 
 // MODE: 0 FIRST (acc = u + dt w), 1 MID (acc += dt w), 2 LAST (u = acc + dt w),
 // 3 ONLY (u = u + dt w).  XL: lines along x (contiguous) or along y/z.
-template <typename VT, int KP, int W, int MODE, bool XL>
+template <typename VT, int KP, int W, int MODE, bool XL, bool TG>
 __global__ void __launch_bounds__(256) axis_step_kernel(const AxisStepArgs a) {
     using TS = typename StepTypes<VT>::S;
     constexpr bool DFM = std::is_same<VT, DF>::value;
@@ -82,15 +82,16 @@ __global__ void __launch_bounds__(256) axis_step_kernel(const AxisStepArgs a) {
 
     // ---- shared memory carve-up ------------------------------------------
     // every segment starts on a 16-byte boundary (8-byte cp.async targets).
-    // Long lines read the tables from global memory (every lane of a warp
-    // reads the same row: one broadcast L1 access) to leave room for lines.
-    const bool tg = a.tables_global != 0;
+    // TG (long lines): the tables are read from global memory (every lane of
+    // a warp reads the same row: one broadcast L1 access) to leave room for
+    // lines.  A compile-time switch, so that staged tables keep shared-memory
+    // loads.
     unsigned char* p = smem_raw;
     SolveSmem<TS> S;
     const VT* Ct;
     const VT* At;
     const int* fs;
-    if (tg) {
+    if constexpr (TG) {
         S = SolveSmem<TS>{LS.L, LS.U, LS.dinv, LS.G, LS.H, LS.PhiF, LS.PhiB};
         if constexpr (DFM) {
             Ct = reinterpret_cast<const VT*>(AX.C.df);
@@ -139,10 +140,11 @@ __global__ void __launch_bounds__(256) axis_step_kernel(const AxisStepArgs a) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     // y/z-lines: lane -> column cl of the block's NL columns, row offset ro of
     // the RPW rows a warp covers per pass
-    const int lgNL = XL ? 0 : __ffs(NL) - 1;
-    const int cl = XL ? 0 : (lane & (NL - 1));
-    const int ro = XL ? 0 : (lane >> lgNL);
-    const int RPW = XL ? 1 : (32 >> lgNL);
+    // (staged tables always come with all 32 columns: lane = column)
+    const int lgNL = (XL || !TG) ? 0 : __ffs(NL) - 1;
+    const int cl = XL ? 0 : (TG ? (lane & (NL - 1)) : lane);
+    const int ro = (XL || !TG) ? 0 : (lane >> lgNL);
+    const int RPW = (XL || !TG) ? 1 : (32 >> lgNL);
     long long l0 = 0, os = 0, rs = 0;
     int nl, x0 = 0;
     if (XL) {
@@ -366,13 +368,12 @@ static cudaError_t run_axis_step(const AxisStepArgs& a0, cudaStream_t st) {
         while (NL > 1 && smem_for(NL, true) > (size_t)lim) NL = xl ? (NL + 1) / 2 : NL / 2;
     }
     a.lines_per_block = NL;
-    a.tables_global = tg ? 1 : 0;
     const size_t sm = smem_for(NL, tg);
     if (sm > (size_t)lim) return cudaErrorInvalidValue;
     // modes 0 (first of several axes) and 3 (1D) run along x, modes 1 and 2 across
     constexpr bool XL = (MODE == 0 || MODE == 3);
     if (xl != XL) return cudaErrorInvalidValue;
-    auto k = axis_step_kernel<VT, KP, W, MODE, XL>;
+    auto k = tg ? axis_step_kernel<VT, KP, W, MODE, XL, true> : axis_step_kernel<VT, KP, W, MODE, XL, false>;
     if (sm > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if constexpr (XL) {
         k<<<(unsigned)((nlines + NL - 1) / NL), 256, sm, st>>>(a);

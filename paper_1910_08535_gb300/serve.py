@@ -103,13 +103,22 @@ def base_state(shape):
 
 
 def slot_bytes(shape):
-    """Device bytes a slot holds (estimate): tensors and scratch at 8 bytes per
-    coefficient, the Poisson source samples and dense 1D transforms."""
+    """Resident device bytes of a slot (estimate): the context's tables and
+    scratch and the slot's tensors at 8 bytes per coefficient, plus the dense
+    1D transforms of a Poisson context."""
     n = shape.n_elem + shape.degree
     b = 6 * 8 * shape.ntot + (4 << 20)
     if shape.kind == 'poisson':
-        b += (8 if shape.precision == 'fp64' else 4) * shape.nquad + shape.dim * 2 * 4 * n * n
+        b += shape.dim * 2 * 4 * n * n
     return b
+
+
+def transient_bytes(shape):
+    """Device bytes a request holds only while it runs: the source samples of
+    a Poisson request (upper bound on the quadrature grid)."""
+    if shape.kind != 'poisson':
+        return 0
+    return (8 if shape.precision == 'fp64' else 4) * shape.nquad
 
 
 class Slot:
@@ -132,7 +141,8 @@ class Slot:
             if shape.kind == 'poisson':
                 self.b = self.ctx.empty()
                 self.qx = [torch.from_numpy(self.ctx.quad_points(a)[0]).to('cuda', hdtype) for a in range(shape.dim)]
-                self.f = torch.empty(tuple(len(q) for q in reversed(self.qx)), dtype=hdtype, device='cuda')
+        self.hdtype = hdtype
+        self.f = None           # source samples: allocated per request, dropped at completion
         self.host_out = torch.empty(planes * self.ctx.ntot, dtype=hdtype).pin_memory()
         if shape.kind == 'heat':
             u0 = base_state(shape).ravel()
@@ -156,6 +166,7 @@ class Slot:
                 self.u.view(-1).copy_(self.host_in, non_blocking=True)
                 self.ctx.step(self.u, req.dt_h2 / (sh.n_elem ** 2 * sh.dim), req.steps)
             else:
+                self.f = torch.empty(tuple(len(q) for q in reversed(self.qx)), dtype=self.hdtype, device='cuda')
                 scale = float(np.pi ** 2 * sum(k * k for k in req.k))
                 fac = [torch.sin((req.k[a] * np.pi) * self.qx[a]) for a in range(sh.dim)]
                 if sh.dim == 2:
@@ -168,6 +179,12 @@ class Slot:
             self.host_out.copy_(self.u.view(-1), non_blocking=True)
             self.done.record(self.stream)
         self.req = req
+
+    def retire(self):
+        """After completion: drop the request's transient buffers (their
+        memory goes back to the stream's allocator cache)."""
+        self.f = None
+        self.req = None
 
     def result(self):
         a = self.host_out.numpy()
@@ -188,7 +205,8 @@ class Server:
         self.budget = budget_bytes
         self.max_inflight = max_inflight
         self.pools = collections.defaultdict(list)   # shape -> idle slots
-        self.used = 0
+        self.used = 0                                # resident bytes of all slots
+        self.transient = 0                           # bytes of the requests in flight
         self.inflight = []
         self.created = 0
         self.evicted = 0
@@ -201,16 +219,19 @@ class Server:
                 self.used -= slot_bytes(sh)
                 self.evicted += 1
 
-    def acquire(self, shape):
-        """An idle slot of `shape`, a new one if the budget allows, else None."""
+    def acquire(self, shape, extra=0):
+        """An idle slot of `shape`, a new one if the budget allows (with
+        `extra` transient bytes on top of what is in flight), else None."""
         if self.pools[shape]:
+            if self.used + self.transient + extra > self.budget:
+                return None
             return self.pools[shape].pop()
         need = slot_bytes(shape)
-        if need > self.budget:
-            raise ValueError(f'request needs {need} bytes, above the whole budget')
-        if self.used + need > self.budget:
-            self._evict_idle(need)
-            if self.used + need > self.budget:
+        if need + extra > self.budget:
+            raise ValueError(f'request needs {need + extra} bytes, above the whole budget')
+        if self.used + self.transient + need + extra > self.budget:
+            self._evict_idle(need + extra + self.transient)
+            if self.used + self.transient + need + extra > self.budget:
                 return None
         s = Slot(shape)
         self.used += need
@@ -233,18 +254,20 @@ class Server:
             # admit arrived requests in order while slots and memory allow
             while pending and pending[0].arrival <= now and len(self.inflight) < self.max_inflight:
                 req = pending[0]
-                slot = self.acquire(req.shape)
+                extra = transient_bytes(req.shape)
+                slot = self.acquire(req.shape, extra)
                 if slot is None:
                     break
                 pending.popleft()
                 admit = clock() - t0
+                self.transient += extra
                 slot.launch(req)
                 records[req.rid] = {'arrival': req.arrival, 'admit': admit, 'kind': req.shape.kind,
                                     'dim': req.shape.dim, 'n_elem': req.shape.n_elem,
                                     'degree': req.shape.degree, 'precision': req.shape.precision,
                                     'dof': req.shape.ntot, 'steps': req.steps if req.shape.kind == 'heat' else 0,
                                     'h2d': slot.h2d_bytes, 'd2h': slot.d2h_bytes,
-                                    'bytes': slot_bytes(req.shape)}
+                                    'bytes': slot_bytes(req.shape) + extra}
                 self.inflight.append(slot)
             # retire finished requests
             still = []
@@ -255,8 +278,9 @@ class Server:
                     rec['latency'] = rec['done'] - rec['arrival']
                     if keep_results:
                         results[s.req.rid] = s.result()
+                    self.transient -= transient_bytes(s.shape)
+                    s.retire()
                     self.pools[s.shape].append(s)
-                    s.req = None
                 else:
                     still.append(s)
             self.inflight = still

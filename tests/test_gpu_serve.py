@@ -65,7 +65,7 @@ def test_mix_equals_alone_and_oracle():
 def test_budget_caps_resident_slots():
     from paper_1910_08535_gb300 import serve
     reqs = _stream(20, seed=11)
-    biggest = max(serve.slot_bytes(r.shape) for r in reqs)
+    biggest = max(serve.slot_bytes(r.shape) + serve.transient_bytes(r.shape) for r in reqs)
     srv = serve.Server(budget_bytes=2 * biggest, max_inflight=16)
     recs, _ = srv.run(reqs)
     srv.check()

@@ -38,10 +38,14 @@ def test_slot_bytes_grow_with_size_and_cover_tensors():
     small = serve.Shape('heat', 2, 64, 2, 'fp64')
     big = serve.Shape('heat', 2, 1024, 2, 'fp64')
     assert serve.slot_bytes(big) > serve.slot_bytes(small) >= 8 * small.ntot
+    assert serve.transient_bytes(big) == 0
     p = serve.Shape('poisson', 3, 160, 3, 'fp64')
-    assert serve.slot_bytes(p) >= 8 * p.nquad
+    # resident: tensors plus the dense 1D transforms; transient: the source samples
+    assert serve.slot_bytes(p) >= 8 * p.ntot + 3 * 2 * 4 * (p.n_elem + p.degree) ** 2
+    assert serve.transient_bytes(p) == 8 * p.nquad
+    assert serve.transient_bytes(serve.Shape('poisson', 3, 160, 3, 'fp32r')) == 4 * p.nquad
     # the largest request of the mixed stream fits the 120 GB budget several times over
-    assert serve.slot_bytes(p) * 5 < 120 * 10 ** 9
+    assert (serve.slot_bytes(p) + serve.transient_bytes(p)) * 5 < 120 * 10 ** 9
 
 
 def test_summary_percentiles():
