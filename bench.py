@@ -33,7 +33,7 @@ METRIC = 'explicit-step DOF-updates/s PW-const vs Galerkin (% HBM peak); served 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument('--gpus', type=int, default=1)
-    ap.add_argument('--steps', type=int, default=5)
+    ap.add_argument('--steps', type=int, default=20)
     ap.add_argument('--warmup', type=int, default=3)
     ap.add_argument('--impl', default='native', choices=['native', 'reference'])
     ap.add_argument('--residual', default='df', choices=['fp64', 'df'])
@@ -85,24 +85,39 @@ class ClockSampler:
         self.proc = None
 
     def __enter__(self):
+        import threading
+        self.lines = []
         try:
             self.proc = subprocess.Popen(
                 ['nvidia-smi', '-i', str(self.index), f'--query-gpu={self.Q}', '--format=csv,noheader,nounits',
-                 '-lms', '100'], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 '-lms', '20'], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except OSError:
             self.proc = None
+            return self
+
+        def reader():
+            for l in self.proc.stdout:
+                if l.strip():
+                    self.lines.append(l)
+
+        self.thread = threading.Thread(target=reader, daemon=True)
+        self.thread.start()
+        # the timed region starts once the sampler is producing samples
+        t0 = time.time()
+        while not self.lines and time.time() - t0 < 5.0 and self.proc.poll() is None:
+            time.sleep(0.01)
+        self.skip = len(self.lines)
         return self
 
     def __exit__(self, *a):
-        self.lines = []
         if self.proc is not None:
             self.proc.terminate()
             try:
-                out, _ = self.proc.communicate(timeout=5)
+                self.proc.wait(timeout=5)
             except subprocess.TimeoutExpired:
                 self.proc.kill()
-                out, _ = self.proc.communicate()
-            self.lines = [l for l in out.splitlines() if l.strip()]
+            self.thread.join(timeout=5)
+            self.lines = self.lines[max(self.skip - 1, 0):]
 
     def summary(self):
         import statistics
@@ -433,8 +448,12 @@ def run_native(args, rank, world):
                 one.append(e0.elapsed_time(e1) / 1e3)
     t_one = sum(one) / len(one)
     pk = peaks()
-    W = 5                                   # PW cubic window (Galerkin: 7)
-    ops_per_dof_axis = 23 * W + 32          # see the design doc: double-float g = C u, residual, 2 FP32 solves, update
+    # FP32 operations per DOF and axis of the double-float split step (FMA = 1):
+    # g = C u, W compensated products of 12 operations + 3 to normalise;
+    # residual g - A w0, W products of 11 + 3; two FP32 banded solves of
+    # 2p + 1 = 7 each; update two-sum 6 + compensated product 12 + 3.
+    W, p = 5, 3                             # PW cubic window (Galerkin: 7)
+    ops_per_dof_axis = 12 * W + 3 + 11 * W + 3 + 2 * (2 * p + 1) + 21
     alg_ops = ntot * 3 * ops_per_dof_axis   # one step = 3 axis launches
     sm_mhz = pk.get('sm_max_mhz', 2070.0)
     alu_peak = 152 * 128 * sm_mhz * 1e6 / 1e12
