@@ -126,7 +126,9 @@ __global__ void __launch_bounds__(256) axis_step_kernel(const AxisStepArgs a) {
     }
     // lines carry W zero rows past n, so the contraction windows need no guards
     const int nr = n + W;
-    const int pitch = XL ? (nr | 1) : NL + 1;
+    // staged y/z blocks always hold 32 columns: a compile-time pitch of 33 turns
+    // the row offsets of the banded windows into immediate offsets
+    const int pitch = XL ? (nr | 1) : (TG ? NL + 1 : 33);
     const int st = XL ? 1 : pitch;      // row stride within a line
     const int lst = XL ? pitch : 1;     // line stride
     const int cap = XL ? NL * pitch : nr * pitch;
@@ -137,7 +139,9 @@ __global__ void __launch_bounds__(256) axis_step_kernel(const AxisStepArgs a) {
     for (int e = threadIdx.x; e < 33; e += blockDim.x) bnd[e] = LS.b[e];
 
     // ---- which lines: global index of (line l, row i) ---------------------
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    // launched with 256 threads (8 warps) always
+    constexpr int nw = 8;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     // y/z-lines: lane -> column cl of the block's NL columns, row offset ro of
     // the RPW rows a warp covers per pass
     // (staged tables always come with all 32 columns: lane = column)
