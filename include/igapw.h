@@ -253,6 +253,53 @@ long long igapw_size(igapw_ctx* ctx, int* dims);
 /* Frees everything the context owns.  Synchronizes its stream first. */
 int igapw_destroy(igapw_ctx* ctx);
 
+/* ---- batched 2D Poisson over many uneven instances ----------------------
+ * The problem of Sec. 4.3 (-Lap u = f, zero Dirichlet rows, Eq. (7) tested
+ * with PW cells or B-splines) for `count` independent 2D instances of
+ * different sizes and degrees, FP32 pairs with one refinement step (as
+ * igapw_solve on a 2D POISSON context).  Each stage runs for all instances
+ * in one launch: the source RHS (a persistent kernel over a work queue of
+ * instance tiles), the fast-diagonalisation transforms (grouped GEMMs), the
+ * double-float residual (persistent kernels, one per window width) and the
+ * elementwise updates; the solve is captured once into a CUDA graph.  The
+ * batch owns the instances' RHS and solution tensors (pair layout, see
+ * igapw_batch_tensor). */
+typedef struct igapw_batch igapw_batch;
+
+/* descs[count]: each dim = 2, op = POISSON, bc = DIRICHLET0, precision =
+ * FP32_REFINE (else IGAPW_ERR_ARG).  Builds one context per instance (tables,
+ * diagonalised pencils), packs their tensors, and times the candidate tile
+ * shapes of the two persistent kernels on the batch, keeping the fastest.
+ * Synchronous. */
+int igapw_batch_create(igapw_batch** out, const igapw_desc* descs, int count, void* cuda_stream);
+
+/* RHS of every instance for the manufactured source
+ * f_i(x, y) = amp_i sin(kx_i pi x) sin(ky_i pi y), evaluated in the kernel at
+ * each instance's quadrature points (FP32, like igapw_rhs_source samples) and
+ * summed over the test supports in double-float.  params: host array of
+ * count x 3 doubles (amp, kx, ky).  Synchronous. */
+int igapw_batch_source_sine(igapw_batch* b, const double* params);
+
+/* u_i = K_i^{-1} b_i for every instance (the batch's RHS tensors, e.g. from
+ * igapw_batch_source_sine or written through igapw_batch_tensor).
+ * Asynchronous on the batch stream (one graph launch). */
+int igapw_batch_solve(igapw_batch* b);
+
+/* Device pointer of instance i's RHS (which = 0) or solution (which = 1):
+ * a pair tensor of 2 * n_total floats owned by the batch. */
+int igapw_batch_tensor(igapw_batch* b, int i, int which, void** dev, long long* n_total);
+
+/* Tile shapes picked by the autotuner: tiles[0..1] source (x, y), tiles[2..3]
+ * residual (x, y). */
+int igapw_batch_info(igapw_batch* b, int* tiles);
+
+/* Message of the last failure on the batch (NULL: the thread's last create
+ * error).  Never NULL. */
+const char* igapw_batch_last_error(igapw_batch* b);
+
+/* Frees the batch and its instances' contexts (synchronizes the stream). */
+int igapw_batch_destroy(igapw_batch* b);
+
 #ifdef __cplusplus
 }
 #endif

@@ -714,4 +714,23 @@ int source_setup(igapw_ctx* c, const void* f_dev, void* b_dev, SourceArgs& a, si
 
 int record_error(igapw_ctx* c, int code, const std::string& msg) { return fail(c, code, msg); }
 
+int ctx_view(igapw_ctx* c, CtxView& v) {
+    if (!c) return IGAPW_ERR_ARG;
+    v.dim = c->dim;
+    v.W = c->W;
+    v.p = c->p;
+    v.precision = c->d.precision;
+    v.op = c->d.op;
+    v.test = c->d.test;
+    v.ntot = c->ntot;
+    for (int a = 0; a < 3; ++a) {
+        v.n[a] = c->n[a];
+        v.ax[a] = c->dev[a];
+        v.qx[a] = a < c->dim ? c->mem[a].qx : nullptr;
+        v.q[a] = a < c->dim ? (int)c->ax[a].qx.size() : 1;
+    }
+    v.fdm = c->fdm;
+    return IGAPW_OK;
+}
+
 }  // namespace igapw

@@ -130,4 +130,17 @@ int source_setup(::igapw_ctx* c, const void* f_dev, void* b_dev, SourceArgs& a, 
                  cudaStream_t& st, bool& f64);
 int record_error(::igapw_ctx* c, int code, const std::string& msg);
 
+// ---- read-only view of a context for the batched entry points (batch.cu) ----
+struct FdmState;
+struct CtxView {
+    int dim, W, p, precision, op, test;
+    int n[3];
+    int q[3];                 // quadrature points per axis
+    long long ntot;
+    AxisDev ax[3];
+    const double* qx[3];      // device quadrature-point coordinates per axis
+    const FdmState* fdm;      // 2D/3D Poisson contexts: spectral data
+};
+int ctx_view(::igapw_ctx* c, CtxView& v);
+
 }  // namespace igapw

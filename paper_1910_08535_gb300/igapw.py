@@ -58,6 +58,13 @@ _SIGS = {
     'igapw_last_error': (ctypes.c_char_p, [_VP]),
     'igapw_size': (ctypes.c_longlong, [_VP, ctypes.POINTER(_I)]),
     'igapw_destroy': (_I, [_VP]),
+    'igapw_batch_create': (_I, [ctypes.POINTER(_VP), ctypes.POINTER(igapw_desc), _I, _VP]),
+    'igapw_batch_source_sine': (_I, [_VP, ctypes.POINTER(_D)]),
+    'igapw_batch_solve': (_I, [_VP]),
+    'igapw_batch_tensor': (_I, [_VP, _I, _I, ctypes.POINTER(_VP), ctypes.POINTER(ctypes.c_longlong)]),
+    'igapw_batch_info': (_I, [_VP, ctypes.POINTER(_I)]),
+    'igapw_batch_last_error': (ctypes.c_char_p, [_VP]),
+    'igapw_batch_destroy': (_I, [_VP]),
 }
 
 _lib = None
@@ -191,6 +198,50 @@ def igapw_destroy(ctx):
     _check(load().igapw_destroy(ctx), None)
 
 
+def _bcheck(rc, b=None):
+    if rc != IGAPW_OK:
+        msg = load().igapw_batch_last_error(b)
+        raise IgapwError(rc, msg.decode() if msg else '')
+
+
+def igapw_batch_create(descs, stream=None):
+    arr = (igapw_desc * len(descs))(*descs)
+    b = ctypes.c_void_p()
+    _bcheck(load().igapw_batch_create(ctypes.byref(b), arr, len(descs), _stream_handle(stream)), None)
+    return b
+
+
+def igapw_batch_source_sine(b, params):
+    import numpy as np
+    p = np.ascontiguousarray(params, dtype=np.float64)
+    _bcheck(load().igapw_batch_source_sine(b, p.ctypes.data_as(ctypes.POINTER(_D))), b)
+
+
+def igapw_batch_solve(b):
+    _bcheck(load().igapw_batch_solve(b), b)
+
+
+def igapw_batch_tensor(b, i, which):
+    ptr = ctypes.c_void_p()
+    n = ctypes.c_longlong()
+    _bcheck(load().igapw_batch_tensor(b, i, which, ctypes.byref(ptr), ctypes.byref(n)), b)
+    return ptr.value, n.value
+
+
+def igapw_batch_info(b):
+    t = (_I * 4)()
+    _bcheck(load().igapw_batch_info(b, t), b)
+    return tuple(t)
+
+
+def igapw_batch_last_error(b):
+    return load().igapw_batch_last_error(b).decode()
+
+
+def igapw_batch_destroy(b):
+    _bcheck(load().igapw_batch_destroy(b), None)
+
+
 # ---- torch convenience wrapper ----------------------------------------------
 
 class Context:
@@ -282,6 +333,71 @@ class Context:
         if self.ctx:
             igapw_destroy(self.ctx)
             self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _desc(dim, n_elem, degree, nq, test, bc, precision, op, flags=0):
+    if isinstance(n_elem, int):
+        n_elem = [n_elem] * dim
+    d = igapw_desc()
+    d.dim = dim
+    for a in range(3):
+        d.n_elem[a] = n_elem[a] if a < dim else 1
+    d.degree, d.nq = degree, nq
+    d.test, d.bc = TESTS[test], BCS[bc]
+    d.precision, d.op, d.flags = PRECISIONS[precision], OPS[op], flags
+    return d
+
+
+class _DevArray:
+    """A device buffer owned by the library, exposed to torch without a copy."""
+
+    def __init__(self, ptr, count):
+        self.__cuda_array_interface__ = {'shape': (count,), 'typestr': '<f4', 'data': (ptr, False), 'version': 2}
+
+
+class Batch:
+    """Batched 2D Poisson instances (FP32 pairs): shapes is a list of
+    (n_elem_x, n_elem_y, degree) tuples; tests PW or Galerkin."""
+
+    def __init__(self, shapes, test='pw', stream=None):
+        import torch
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.shapes = [tuple(s) for s in shapes]
+        descs = [_desc(2, [nx, ny], p, p + 1, test, 'dirichlet0', 'fp32r', 'poisson') for nx, ny, p in self.shapes]
+        self.handle = igapw_batch_create(descs, self.stream)
+
+    def source_sine(self, params):
+        igapw_batch_source_sine(self.handle, params)
+
+    def solve(self):
+        igapw_batch_solve(self.handle)
+
+    def tensor(self, i, which):
+        """Instance i's RHS (which = 0) or solution (1) as a torch view of shape
+        (2, n_y, n_x) (hi plane, lo plane), aliasing the batch's memory."""
+        import torch
+        ptr, n = igapw_batch_tensor(self.handle, i, which)
+        nx, ny, p = self.shapes[i]
+        t = torch.as_tensor(_DevArray(ptr, 2 * n), device='cuda')
+        return t.view(2, ny + p, nx + p)
+
+    def to_numpy(self, i, which):
+        t = self.tensor(i, which).cpu().numpy().astype('float64')
+        return t[0] + t[1]
+
+    def tiles(self):
+        return igapw_batch_info(self.handle)
+
+    def close(self):
+        if self.handle:
+            igapw_batch_destroy(self.handle)
+            self.handle = None
 
     def __del__(self):
         try:

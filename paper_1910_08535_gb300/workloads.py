@@ -92,6 +92,19 @@ def sine_product_exact(k):
     return u
 
 
+def batch_shapes(count, seed=0, lo=32, hi=512, rungs=16):
+    """Shapes (n_elem_x, n_elem_y, degree) of a batch of square 2D instances:
+    N log-uniform on `rungs` geometric rungs from lo to hi, degree uniform in
+    {2, 3}."""
+    ladder = np.unique(np.round(np.geomspace(lo, hi, rungs)).astype(int))
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for _ in range(count):
+        n = int(ladder[int(rng.integers(0, len(ladder)))])
+        out.append((n, n, int(rng.integers(2, 4))))
+    return out
+
+
 def initial_state(name, seed=0):
     w = WORKLOADS[name]
     n = w['n_elem'] + w['degree']

@@ -54,3 +54,12 @@ def test_summary_percentiles():
     s = serve.summarize(recs)
     assert abs(s['p50_ms'] - 50.5) < 1e-9 and abs(s['p99_ms'] - 99.01) < 1e-9
     assert s['requests'] == 100 and s['h2d_bytes'] == 800
+
+
+def test_batch_shapes_ladder():
+    from paper_1910_08535_gb300 import workloads
+    s = workloads.batch_shapes(512, seed=0)
+    assert len(s) == 512 and s == workloads.batch_shapes(512, seed=0)
+    ns = sorted({a for a, _, _ in s})
+    assert ns[0] == 32 and ns[-1] == 512 and len(ns) <= 16
+    assert all(a == b for a, b, _ in s) and {p for _, _, p in s} == {2, 3}
