@@ -353,6 +353,61 @@ def measure_serving(requests=2000, seed=6, budget=120 * 10 ** 9):
     return out
 
 
+def measure_batch(stream, count=512, seed=0, reps=10):
+    """Row a8 (batched 2D Poisson, 512 uneven instances): N log-uniform on 16
+    rungs in [32, 512] per axis, p in {2, 3}, PW tests, FP32 pairs with one
+    refinement; manufactured sources amp sin(k1 pi x) sin(k2 pi y), k uniform in
+    1..4.  Times the fused source kernel and the graph-captured batch solve."""
+    import numpy as np
+    import torch
+    from paper_1910_08535_gb300 import workloads
+    from paper_1910_08535_gb300.igapw import Batch
+    shapes = workloads.batch_shapes(count, seed=seed)
+    rng = np.random.Generator(np.random.PCG64(seed))
+    k = rng.integers(1, 5, size=(count, 2))
+    par = np.stack([np.pi ** 2 * (k[:, 0] ** 2 + k[:, 1] ** 2), k[:, 0], k[:, 1]], 1).astype(np.float64)
+    with torch.cuda.stream(stream):
+        t0 = time.perf_counter()
+        bt = Batch(shapes, stream=stream)
+        t_create = time.perf_counter() - t0
+        t_src = _time_events(stream, lambda: bt.source_sine(par), reps)
+        t_solve = _time_events(stream, bt.solve, reps)
+    dof = sum((a + p) * (b + p) for a, b, p in shapes)
+    flops = sum(2 * 2 * 2 * ((a + p) + (b + p)) * (a + p) * (b + p) for a, b, p in shapes)
+    out = {'instances': count, 'dof': dof, 'create_s': t_create, 'tiles_source_residual': bt.tiles(),
+           'source_us': t_src * 1e6, 'solve_us': t_solve * 1e6, 'instances_per_s': count / t_solve,
+           'dof_per_s': dof / t_solve, 'gemm_tflops': flops / t_solve / 1e12,
+           'shapes_sample': shapes[:4], 'params': par, 'batch': bt}
+    return out
+
+
+def cpu_baseline_batch(res, sample=8):
+    """Oracle side of row a8: sampled instances' solutions against the oracle
+    (backward error) and the oracle's sparse direct solve timed per instance."""
+    import numpy as np
+    from oracle import poisson_nd, systems
+    from paper_1910_08535_gb300 import workloads
+    bt, par = res.pop('batch'), res.pop('params')
+    shapes = workloads.batch_shapes(res['instances'], seed=0)
+    idx = np.random.Generator(np.random.PCG64(1)).choice(len(shapes), size=sample, replace=False)
+    etas, secs = [], []
+    for i in idx:
+        nx, ny, p = shapes[i]
+        axes = [systems.Axis(nx, p, p + 1, 'pw', 'dirichlet0'), systems.Axis(ny, p, p + 1, 'pw', 'dirichlet0')]
+        b = bt.to_numpy(int(i), 0)
+        etas.append(poisson_nd.backward_error(axes, bt.to_numpy(int(i), 1), b))
+        if nx <= 200:        # the sparse direct solve of the largest grids takes minutes
+            t0 = time.perf_counter()
+            poisson_nd.solve(axes, b, sparse=True)
+            secs.append((time.perf_counter() - t0, (nx + p) * (ny + p)))
+    bt.close()
+    res['max_backward_error_sample'] = float(max(etas))
+    res['oracle_sparse_direct_dof_per_s_sample'] = (float(sum(d for _, d in secs) / sum(t for t, _ in secs))
+                                                    if secs else None)
+    res['oracle_sample'] = f'{sample} random instances of the batch (sparse direct timing on those with N <= 200)'
+    return res
+
+
 def cpu_baseline_poisson(res):
     """Oracle side of row a7: the backward error of the GPU solutions at full
     size (the oracle applies K by per-axis contractions; a sparse direct
@@ -487,6 +542,7 @@ def run_native(args, rank, world):
     rows['a4_source_table1'] = measure_source_table1(stream, flush, hbm_peak)
     poisson = measure_poisson(stream, flush)
     rows['a7_poisson_2d_1024'] = cpu_baseline_poisson(poisson)
+    rows['a8_batch_poisson_512'] = cpu_baseline_batch(measure_batch(stream))
     # the request server is a one-GPU process: measured at N = 1
     serving = measure_serving() if (world == 1 and not args.no_serve) else None
 

@@ -1,0 +1,70 @@
+"""Small, self-contained runs of the hot kernels for profiler captures (ncu
+`-k`/`-c` filters pick the launches):
+
+  python -m paper_1910_08535_gb300.profile_cases heat3d-step   # 3 explicit steps, 131^3, PW, FP32 pairs
+  python -m paper_1910_08535_gb300.profile_cases poisson2d     # 3 solves, 2D 1024^2, cubic PW, FP32 pairs
+  python -m paper_1910_08535_gb300.profile_cases batch512      # 2 batched solves, 512 uneven 2D instances
+
+Each case builds the library if needed, runs on cuda:0 and prints 'ok'.
+"""
+import sys
+
+
+def heat3d_step():
+    from . import workloads
+    from .igapw import Context
+    w = workloads.WORKLOADS['heat3d']
+    c = Context(dim=3, n_elem=w['n_elem'], degree=w['degree'], nq=w['nq'], test='pw', precision='fp32r')
+    u = c.from_numpy(workloads.initial_state('heat3d'))
+    for _ in range(3):
+        c.step(u, workloads.dt_of('heat3d'), 1)
+    c.sync()
+    c.close()
+
+
+def poisson2d():
+    import numpy as np
+    import torch
+    from . import workloads
+    from .igapw import Context
+    c = Context(dim=2, n_elem=1024, degree=3, nq=4, test='pw', precision='fp32r', op='poisson', bc='dirichlet0')
+    pts = [c.quad_points(a)[0] for a in range(2)]
+    f = torch.from_numpy(workloads.sine_product_source(pts, (1, 2)).astype(np.float32)).cuda()
+    b = c.rhs_source(f)
+    u = c.empty()
+    for _ in range(3):
+        c.solve(b, out=u)
+    c.sync()
+    c.close()
+
+
+def batch512():
+    import numpy as np
+    from . import workloads
+    from .igapw import Batch
+    shapes = workloads.batch_shapes(512, seed=0)
+    par = np.array([[np.pi ** 2 * 2, 1, 1]] * len(shapes), dtype=np.float64)
+    bt = Batch(shapes)
+    bt.source_sine(par)
+    for _ in range(2):
+        bt.solve()
+    bt.to_numpy(0, 1)
+    bt.close()
+
+
+CASES = {'heat3d-step': heat3d_step, 'poisson2d': poisson2d, 'batch512': batch512}
+
+
+def main(argv):
+    from . import _build
+    _build.build()
+    if len(argv) != 1 or argv[0] not in CASES:
+        print('usage: python -m paper_1910_08535_gb300.profile_cases {' + ','.join(CASES) + '}')
+        return 2
+    CASES[argv[0]]()
+    print('ok')
+    return 0
+
+
+if __name__ == '__main__':
+    sys.exit(main(sys.argv[1:]))
