@@ -104,10 +104,13 @@ typedef struct igapw_ctx igapw_ctx;
  * selects the matrix igapw_solve inverts (POISSON: -Lap u with bc = DIRICHLET0
  * required -- in 1D the banded 1D operator, in 2D/3D the multi-D operator;
  * anything else: the tensor-product mass matrix); flags = IGAPW_FLAG_*.
+ * With neumann_axes, the operator rows of a Neumann axis get the boundary
+ * term [T du/dn] of Sec. 4.3 (-int T B'' + T(b) B'(b) - T(a) B'(a) along that
+ * axis) and every coefficient on it is an unknown.
  * A 2D/3D POISSON context also diagonalises every 1D pencil (L_a, A_a) at
  * creation (FP64 LU and nonsymmetric eigensolver through cuSOLVER, O(n_a^3));
  * creation fails with IGAPW_ERR_ARG if a pencil's spectrum is not real and
- * positive. */
+ * positive (non-negative on a Neumann axis). */
 typedef struct {
     int dim;
     int n_elem[3];
@@ -118,6 +121,9 @@ typedef struct {
     int precision;
     int op;
     int flags;
+    int neumann_axes;   /* POISSON, 2D/3D: bit a set = axis a carries Neumann data on both
+                           of its end faces instead of zero Dirichlet rows (Sec. 4.3 mixed
+                           boundary conditions); at least one axis must stay Dirichlet */
 } igapw_desc;
 
 /* Builds knots, Gauss rules and PW cells on the host, evaluates the basis by
@@ -195,6 +201,16 @@ int igapw_rhs_source_noalloc(igapw_ctx* ctx, const void* f_dev, void* b_dev);
  * sum_a (-int T B'' along a) (x) (int T B along the other axes) on the
  * others. Asynchronous. */
 int igapw_apply(igapw_ctx* ctx, int op, double dt, const void* u_dev, void* r_dev);
+
+/* Neumann data term of Sec. 4.3: b += int over the end face (side 0: x_a = 0
+ * end, 1: the far end) of a Neumann axis of T G, for G sampled on the tensor
+ * grid of the other axes' quadrature points (igapw_quad_points; x fastest among
+ * them; FP64 samples, or FP32 in FP32_REFINE contexts).  With the tests' end
+ * values T_i(end) = 1 for the end row only (PW end cells and open-knot
+ * B-splines alike), this adds the face's 1D-tested data to the rows whose
+ * index on `axis` is the end.  Dirichlet rows stay untouched.  b_dev is a
+ * context tensor (accumulated in place).  Asynchronous. */
+int igapw_rhs_neumann(igapw_ctx* ctx, int axis, int side, const void* g_dev, void* b_dev);
 
 /* Exports one 1D matrix of an axis as a dense row-major n x n double array in
  * host memory: which = IGAPW_OP_MASS (int T_i B_j), IGAPW_OP_LAPLACE

@@ -72,6 +72,22 @@ def assemble(axes, neumann):
     return K
 
 
+def assemble_sparse(axes, neumann):
+    """The same matrix as a scipy CSR matrix (medium meshes)."""
+    import scipy.sparse as sp
+    from .poisson_nd import boundary_mask
+    K = None
+    for t in operator_terms(axes, neumann):
+        term = sp.csr_matrix(np.ones((1, 1)))
+        for M in reversed(t):
+            term = sp.kron(term, sp.csr_matrix(M), format='csr')
+        K = term if K is None else K + term
+    mask = boundary_mask(axes).ravel()
+    K = (sp.diags((~mask).astype(np.float64)) @ K + sp.diags(mask.astype(np.float64))).tocsr()
+    K.eliminate_zeros()
+    return K
+
+
 def apply(axes, neumann, u):
     from .poisson_nd import boundary_mask
     u = np.asarray(u, dtype=np.float64)
@@ -114,9 +130,7 @@ def rhs(axes, neumann, f_grid, faces):
 
 def solve(axes, neumann, b, sparse=False):
     b = np.asarray(b, dtype=np.float64)
-    K = assemble(axes, neumann)
     if sparse:
-        import scipy.sparse as sp
         import scipy.sparse.linalg as spl
-        return spl.spsolve(sp.csc_matrix(K), b.ravel()).reshape(b.shape)
-    return np.linalg.solve(K, b.ravel()).reshape(b.shape)
+        return spl.spsolve(assemble_sparse(axes, neumann).tocsc(), b.ravel()).reshape(b.shape)
+    return np.linalg.solve(assemble(axes, neumann), b.ravel()).reshape(b.shape)

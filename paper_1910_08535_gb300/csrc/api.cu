@@ -20,6 +20,7 @@ struct AxisMem {
     double *knots = nullptr, *qx = nullptr, *qw = nullptr, *vals = nullptr;
     int *qfirst = nullptr, *fstart = nullptr, *pstart = nullptr, *pcount = nullptr, *is_free = nullptr;
     double *A = nullptr, *C = nullptr, *S = nullptr, *TW = nullptr;
+    double *dleft = nullptr, *dright = nullptr;
     float2 *Adf = nullptr, *Cdf = nullptr, *Sdf = nullptr, *TWdf = nullptr;
     double *band = nullptr, *L = nullptr, *U = nullptr, *dinv = nullptr, *G = nullptr, *H = nullptr,
            *PhiF = nullptr, *PhiB = nullptr;
@@ -128,6 +129,18 @@ int build_axis_device(igapw_ctx* c, int a) {
     CKC(c, upload(c, &m.pstart, s.pstart));
     CKC(c, upload(c, &m.pcount, s.pcount));
     CKC(c, upload(c, &m.is_free, s.is_free));
+    CKC(c, upload(c, &m.dleft, s.dleft));
+    CKC(c, upload(c, &m.dright, s.dright));
+    const int neumann = (c->d.neumann_axes >> a) & 1;
+    if (neumann) {
+        // the end rows' windows must hold every column with a non-zero end derivative
+        for (int j = 0; j < n; ++j) {
+            if (s.dleft[j] != 0.0 && (j < s.fstart[0] || j >= s.fstart[0] + W))
+                return fail(c, IGAPW_ERR_ARG, "Neumann term outside the first row's window");
+            if (s.dright[j] != 0.0 && (j < s.fstart[n - 1] || j >= s.fstart[n - 1] + W))
+                return fail(c, IGAPW_ERR_ARG, "Neumann term outside the last row's window");
+        }
+    }
     CKC(c, dalloc(c, &m.vals, (size_t)Q * (p + 1) * 3));
     const size_t nw = (size_t)n * W, nt = (size_t)n * WQ;
     CKC(c, dalloc(c, &m.A, nw)); CKC(c, dalloc(c, &m.C, nw)); CKC(c, dalloc(c, &m.S, nw));
@@ -147,6 +160,7 @@ int build_axis_device(igapw_ctx* c, int a) {
     launch_basis_table(m.knots, p, Q, m.qx, m.qfirst, m.vals, c->stream);
     FoldArgs f{};
     f.n = n; f.p = p; f.W = W; f.WQ = WQ; f.test = s.test; f.poisson = (c->d.op == IGAPW_OP_POISSON && c->dim == 1);
+    f.neumann = neumann; f.dleft = m.dleft; f.dright = m.dright;
     f.fstart = m.fstart; f.pstart = m.pstart; f.pcount = m.pcount; f.is_free = m.is_free;
     f.qfirst = m.qfirst; f.qw = m.qw; f.vals = m.vals;
     f.A = m.A; f.C = m.C; f.S = m.S; f.TW = m.TW;
@@ -313,6 +327,17 @@ int valid_desc(const igapw_desc* d, std::string& why) {
         why = "the POISSON system needs Dirichlet rows";
         return 0;
     }
+    if (d->neumann_axes) {
+        const int all = (1 << d->dim) - 1;
+        if (d->op != IGAPW_OP_POISSON || d->dim < 2) {
+            why = "Neumann axes are supported for the 2D/3D POISSON system";
+            return 0;
+        }
+        if ((d->neumann_axes & ~all) || (d->neumann_axes & all) == all) {
+            why = "neumann_axes must name axes of the problem and leave at least one Dirichlet axis";
+            return 0;
+        }
+    }
     return 1;
 }
 
@@ -328,6 +353,11 @@ int alloc_scratch(igapw_ctx* c) {
         CKC(c, dalloc(c, &c->rho, nt));
     }
     return IGAPW_OK;
+}
+
+// Boundary rows of axis a: a Neumann axis has none (every coefficient is free).
+int axis_bc(const igapw_desc& d, int a) {
+    return ((d.neumann_axes >> a) & 1) ? IGAPW_BC_NONE : d.bc;
 }
 
 // Multi-D Poisson contexts: diagonalise the 1D pencils of every axis (poisson.cu).
@@ -346,6 +376,7 @@ int build_fdm(igapw_ctx* c) {
         CKC(c, cudaMemcpy(in[a].C.data(), c->mem[a].C, in[a].C.size() * 8, cudaMemcpyDeviceToHost));
         in[a].fstart = s.fstart;
         in[a].is_free = s.is_free;
+        in[a].neumann = (c->d.neumann_axes >> a) & 1;
         fr[a] = c->mem[a].is_free;
     }
     c->fdm = new (std::nothrow) FdmState();
@@ -363,7 +394,7 @@ int setup_all(igapw_ctx* c, const std::vector<double>* knots_override, int overr
         std::vector<double> kn;
         if (knots_override && a == override_axis) kn = *knots_override;
         else if (!c->ax[a].knots.empty() && c->ax[a].n_elem == d.n_elem[a] && knots_override) kn = c->ax[a].knots;
-        std::string e = build_axis(c->ax[a], d.n_elem[a], d.degree, d.nq, d.test, d.bc, kn);
+        std::string e = build_axis(c->ax[a], d.n_elem[a], d.degree, d.nq, d.test, axis_bc(d, a), kn);
         if (!e.empty()) return fail(c, IGAPW_ERR_ARG, "axis " + std::to_string(a) + ": " + e);
         wmax = std::max(wmax, c->ax[a].w);
         wqmax = std::max(wqmax, c->ax[a].wq);
@@ -441,7 +472,7 @@ int igapw_set_knots(igapw_ctx* c, int axis, const double* knots, int len) {
     CKC(c, cudaStreamSynchronize(c->stream));
     std::vector<double> kn(knots, knots + len);
     AxisSetup trial;
-    std::string e = build_axis(trial, c->d.n_elem[axis], c->d.degree, c->d.nq, c->d.test, c->d.bc, kn);
+    std::string e = build_axis(trial, c->d.n_elem[axis], c->d.degree, c->d.nq, c->d.test, axis_bc(c->d, axis), kn);
     if (!e.empty()) return fail(c, IGAPW_ERR_ARG, e);
     // rebuild every axis (the padded window width is shared); keep other axes' knots
     std::vector<std::vector<double>> keep(3);
@@ -453,7 +484,7 @@ int igapw_set_knots(igapw_ctx* c, int axis, const double* knots, int len) {
     CKC(c, cudaMemsetAsync(c->status, 0, sizeof(unsigned), c->stream));
     int wmax = 0, wqmax = 0;
     for (int a = 0; a < c->dim; ++a) {
-        std::string err = build_axis(c->ax[a], c->d.n_elem[a], c->d.degree, c->d.nq, c->d.test, c->d.bc, keep[a]);
+        std::string err = build_axis(c->ax[a], c->d.n_elem[a], c->d.degree, c->d.nq, c->d.test, axis_bc(c->d, a), keep[a]);
         if (!err.empty()) return fail(c, IGAPW_ERR_ARG, err);
         wmax = std::max(wmax, c->ax[a].w);
         wqmax = std::max(wqmax, c->ax[a].wq);
@@ -532,6 +563,29 @@ int igapw_rhs_source(igapw_ctx* c, const void* f_dev, void* b_dev) {
     a.ntot = c->ntot;
     cudaError_t e = launch_source(a, fp64(c), c->stream);
     if (e != cudaSuccess) return fail(c, IGAPW_ERR_CUDA, std::string("source: ") + cudaGetErrorString(e));
+    return IGAPW_OK;
+}
+
+int igapw_rhs_neumann(igapw_ctx* c, int axis, int side, const void* g_dev, void* b_dev) {
+    if (!c) return fail(nullptr, IGAPW_ERR_ARG, "ctx is NULL");
+    if (!g_dev || !b_dev) return fail(c, IGAPW_ERR_ARG, "NULL tensor");
+    if (axis < 0 || axis >= c->dim || !((c->d.neumann_axes >> axis) & 1))
+        return fail(c, IGAPW_ERR_ARG, "axis is not a Neumann axis of this context");
+    if (side != 0 && side != 1) return fail(c, IGAPW_ERR_ARG, "side must be 0 or 1");
+    NeumannArgs a{};
+    a.dim = c->dim;
+    a.axis = axis;
+    a.side = side;
+    for (int k = 0; k < 3; ++k) {
+        a.n[k] = c->n[k];
+        a.q[k] = k < c->dim ? (int)c->ax[k].qx.size() : 1;
+        a.ax[k] = c->dev[k];
+    }
+    a.g = g_dev;
+    a.b = b_dev;
+    a.ntot = c->ntot;
+    cudaError_t e = launch_neumann(a, fp64(c), c->stream);
+    if (e != cudaSuccess) return fail(c, IGAPW_ERR_CUDA, std::string("Neumann term: ") + cudaGetErrorString(e));
     return IGAPW_OK;
 }
 

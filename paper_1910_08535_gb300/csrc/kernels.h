@@ -14,6 +14,9 @@ namespace igapw {
 
 struct FoldArgs {
     int n, p, W, WQ, test, poisson;
+    int neumann;                 // add the Neumann boundary term to C (rows 0 and n-1)
+    const double* dleft;         // [n] B_j'(a)
+    const double* dright;        // [n] B_j'(b)
     const int* fstart;
     const int* pstart;
     const int* pcount;
@@ -86,6 +89,19 @@ struct SourceArgs {
     long long ntot;
 };
 cudaError_t launch_source(const SourceArgs& a, int fp64, cudaStream_t st);
+
+// b += face term of a Neumann axis: sum over the other axes' point windows of
+// their test weights times g, added to the rows at the axis end.
+struct NeumannArgs {
+    int dim, axis, side;
+    int n[3];
+    int q[3];
+    AxisDev ax[3];
+    const void* g;          // F64 or F32 samples on the other axes' point grid
+    void* b;                // F64 or PAIR
+    long long ntot;
+};
+cudaError_t launch_neumann(const NeumannArgs& a, int fp64, cudaStream_t st);
 
 // ---- line solves (solve.cu) -------------------------------------------------
 // Solves along one axis of a (n_z, n_y, n_x) tensor with the axis' LU.

@@ -309,7 +309,10 @@ int build_axis(FdmAxisData& out, int a, const FdmAxisInput& in, Scratch& S, cubl
         lmin = std::fmin(lmin, z.x);
         imax = std::fmax(imax, std::fabs(z.y));
     }
-    if (imax > 1e-9 * lmax || !(lmin > 0.0)) {
+    // a Neumann pencil annihilates the constants (one zero eigenvalue, up to
+    // rounding); a Dirichlet axis elsewhere keeps every sum of eigenvalues positive
+    const double lfloor = in.neumann ? -1e-9 * lmax : 0.0;
+    if (imax > 1e-9 * lmax || !(lmin > lfloor)) {
         err = "1D pencil spectrum not real and positive (max |imag| " + std::to_string(imax) + ", min real " +
               std::to_string(lmin) + ")";
         return -1;
@@ -401,6 +404,8 @@ std::string cache_key(int device, const FdmAxisInput& in) {
     put(in.C.data(), in.C.size() * sizeof(double));
     put(in.fstart.data(), in.fstart.size() * sizeof(int));
     put(in.is_free.data(), in.is_free.size() * sizeof(int));
+    const char nm = in.neumann ? 1 : 0;
+    put(&nm, 1);
     return k;
 }
 

@@ -17,6 +17,7 @@ struct FdmAxisInput {
     int n = 0, W = 0;
     std::vector<double> A, C;        // int T_i B_j, int T_i B_j'' (Dirichlet rows: A identity, C 0)
     std::vector<int> fstart, is_free;
+    bool neumann = false;            // Neumann axis: the pencil has the constants as a zero mode
 };
 
 // Spectral data of one 1D pencil, embedded in the full index range [0, n):

@@ -1,5 +1,7 @@
 // Kernel (b): contraction launch dispatch (operator, system and residual
 // modes; the kernel template is in contract.cuh) and the source RHS kernels.
+#include <type_traits>
+
 #include "contract.cuh"
 
 namespace igapw {
@@ -143,6 +145,77 @@ __global__ void __launch_bounds__(256) source_pw_kernel(const SourceArgs a) {
         ((float*)a.out)[e] = r.hi;
         ((float*)a.out)[e + a.ntot] = r.lo;
     }
+}
+
+// ---------------------------------------------------------------------------
+// Neumann face term (Sec. 4.3): for every coefficient of the end face of a
+// Neumann axis, the tests of the other axes (their point windows, PW or
+// B-spline) applied to the face data g, added to the end row (the only test
+// that is non-zero at the end).  One thread per face coefficient.
+// ---------------------------------------------------------------------------
+template <typename CT, int IN_F32>
+__global__ void __launch_bounds__(256) neumann_face_kernel(const NeumannArgs a) {
+    int o[2] = {0, 0};
+    int no = 0;
+    for (int k = 0; k < a.dim; ++k)
+        if (k != a.axis) o[no++] = k;
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int n0 = a.n[o[0]], n1 = no > 1 ? a.n[o[1]] : 1;
+    if (e >= (long long)n0 * n1) return;
+    const int i0 = (int)(e % n0), i1 = (int)(e / n0);
+    const AxisDev& A0 = a.ax[o[0]];
+    const int w0 = A0.wq, ps0 = A0.pstart[i0], Q0 = a.q[o[0]];
+    const int w1 = no > 1 ? a.ax[o[1]].wq : 1, ps1 = no > 1 ? a.ax[o[1]].pstart[i1] : 0;
+    const int Q1 = no > 1 ? a.q[o[1]] : 1;
+    Acc<CT> acc;
+    acc.init();
+    for (int c1 = 0; c1 < w1; ++c1) {
+        const int q1 = ps1 + c1;
+        if (q1 >= Q1) break;
+        const CT t1 = no > 1 ? tab<CT>(a.ax[o[1]].TW, i1 * w1 + c1) : from_double<CT>(1.0);
+        Acc<CT> s0;
+        s0.init();
+        for (int c0 = 0; c0 < w0; ++c0) {
+            const int q0 = ps0 + c0;
+            if (q0 >= Q0) break;
+            const CT tw = tab<CT>(A0.TW, i0 * w0 + c0);
+            const long long gi = (long long)q1 * Q0 + q0;
+            if constexpr (std::is_same<CT, double>::value) {
+                s0.add_prod(tw, IN_F32 ? (double)((const float*)a.g)[gi] : ((const double*)a.g)[gi]);
+            } else {
+                s0.add_prod_f(tw, ((const float*)a.g)[gi]);
+            }
+        }
+        acc.add_prod(t1, s0.result());
+    }
+    int idx[3] = {0, 0, 0};
+    idx[o[0]] = i0;
+    if (no > 1) idx[o[1]] = i1;
+    idx[a.axis] = a.side ? a.n[a.axis] - 1 : 0;
+    const long long g = ((long long)idx[2] * a.n[1] + idx[1]) * a.n[0] + idx[0];
+    const CT r = acc.result();
+    if constexpr (std::is_same<CT, double>::value) {
+        ((double*)a.b)[g] += r;
+    } else {
+        float* b = (float*)a.b;
+        DFAcc t;
+        t.s = b[g];
+        t.c = b[g + a.ntot];
+        t.add(r);
+        const DF v = t.result();
+        b[g] = v.hi;
+        b[g + a.ntot] = v.lo;
+    }
+}
+
+cudaError_t launch_neumann(const NeumannArgs& a, int fp64, cudaStream_t st) {
+    long long face = 1;
+    for (int k = 0; k < a.dim; ++k)
+        if (k != a.axis) face *= a.n[k];
+    const unsigned blocks = (unsigned)((face + 255) / 256);
+    if (fp64) neumann_face_kernel<double, 0><<<blocks, 256, 0, st>>>(a);
+    else neumann_face_kernel<DF, 1><<<blocks, 256, 0, st>>>(a);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_source(const SourceArgs& a, int fp64, cudaStream_t st) {

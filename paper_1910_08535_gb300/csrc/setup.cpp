@@ -57,6 +57,47 @@ static std::string fmt(const char* f, int a, int b = 0) {
     return buf;
 }
 
+// Values of the k+1 degree-k B-splines that are non-zero on knot span s
+// (t[s] <= x <= t[s+1]) at x: N[r] = B_{s-k+r,k}(x), r = 0..k (the standard
+// triangular Cox--de Boor evaluation).
+static void span_values(const std::vector<double>& t, int s, int k, double x, double* N) {
+    double left[8], right[8];
+    N[0] = 1.0;
+    for (int j = 1; j <= k; ++j) {
+        left[j] = x - t[s + 1 - j];
+        right[j] = t[s + j] - x;
+        double saved = 0.0;
+        for (int r = 0; r < j; ++r) {
+            const double den = right[r + 1] + left[j - r];
+            const double tmp = den != 0.0 ? N[r] / den : 0.0;
+            N[r] = saved + right[r + 1] * tmp;
+            saved = left[j - r] * tmp;
+        }
+        N[j] = saved;
+    }
+}
+
+// B_j'(x) for all j at an end of the axis: B'_{j,p} = p (B_{j,p-1} / (t_{j+p} - t_j)
+// - B_{j+1,p-1} / (t_{j+p+1} - t_{j+1})) with the degree p-1 values of span s.
+static void end_derivs(const AxisSetup& ax, int s, double x, std::vector<double>& d) {
+    const int p = ax.p, n = ax.n;
+    const std::vector<double>& t = ax.knots;
+    double N[8];
+    span_values(t, s, p - 1, x, N);
+    auto lower = [&](int j) {   // B_{j,p-1}(x)
+        const int r = j - (s - (p - 1));
+        return (r >= 0 && r <= p - 1) ? N[r] : 0.0;
+    };
+    d.assign(n, 0.0);
+    for (int j = 0; j < n; ++j) {
+        double v = 0.0;
+        const double d1 = t[j + p] - t[j], d2 = t[j + p + 1] - t[j + 1];
+        if (d1 > 0.0) v += lower(j) / d1;
+        if (d2 > 0.0) v -= lower(j + 1) / d2;
+        d[j] = p * v;
+    }
+}
+
 std::string build_axis(AxisSetup& ax, int n_elem, int p, int nq, int test, int bc,
                        const std::vector<double>& knots_in) {
     ax = AxisSetup();
@@ -211,6 +252,10 @@ std::string build_axis(AxisSetup& ax, int n_elem, int p, int nq, int test, int b
 
     // ---- chunks of the partitioned line solve: P <= 32, length >= p -------
     set_chunks(ax, 1);
+    // end derivatives: left end on the first non-empty span (s = p), right end
+    // on the last (s = n - 1), evaluated at the end point itself
+    end_derivs(ax, p, ax.knots[0], ax.dleft);
+    end_derivs(ax, n - 1, ax.knots[n + p], ax.dright);
     return "";
 }
 

@@ -41,6 +41,10 @@ struct AxisSetup {
 
     // PW cell break points (empty for Galerkin)
     std::vector<double> cells;
+
+    // first derivatives of every basis function at the two ends of the axis
+    // (the Neumann boundary term of Sec. 4.3 uses them)
+    std::vector<double> dleft, dright;
 };
 
 // Builds everything for one axis from (n_elem, p, nq, test, bc) and optional

@@ -109,6 +109,13 @@ __global__ void fold_kernel(FoldArgs f) {
                 sc += tw * f.vals[((size_t)q * (f.p + 1) + a) * 3 + 2];
             }
         }
+        // Neumann axis (Sec. 4.3): the operator row is -C + E with
+        // E_ij = T_i(b) B_j'(b) - T_i(a) B_j'(a); the end rows hold the tests
+        // that are 1 at the ends, so C_ij -= E_ij on rows 0 and n-1
+        if (f.neumann && j < f.n) {
+            if (i == f.n - 1) sc -= f.dright[j];
+            if (i == 0) sc += f.dleft[j];
+        }
         double ss = sa;
         if (f.poisson) ss = f.is_free[i] ? -sc : sa;
         f.A[tid] = sa;

@@ -38,7 +38,8 @@ class IgapwError(RuntimeError):
 class igapw_desc(ctypes.Structure):
     _fields_ = [('dim', ctypes.c_int), ('n_elem', ctypes.c_int * 3), ('degree', ctypes.c_int),
                 ('nq', ctypes.c_int), ('test', ctypes.c_int), ('bc', ctypes.c_int),
-                ('precision', ctypes.c_int), ('op', ctypes.c_int), ('flags', ctypes.c_int)]
+                ('precision', ctypes.c_int), ('op', ctypes.c_int), ('flags', ctypes.c_int),
+                ('neumann_axes', ctypes.c_int)]
 
 
 _VP, _I, _D = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
@@ -49,6 +50,7 @@ _SIGS = {
     'igapw_basis_table': (_I, [_VP, _I, ctypes.POINTER(_D), ctypes.POINTER(_I)]),
     'igapw_rhs_source': (_I, [_VP, _VP, _VP]),
     'igapw_rhs_source_noalloc': (_I, [_VP, _VP, _VP]),
+    'igapw_rhs_neumann': (_I, [_VP, _I, _I, _VP, _VP]),
     'igapw_apply': (_I, [_VP, _I, _D, _VP, _VP]),
     'igapw_assemble_1d': (_I, [_VP, _I, _I, ctypes.POINTER(_D)]),
     'igapw_solve': (_I, [_VP, _VP, _VP]),
@@ -157,6 +159,10 @@ def igapw_rhs_source_noalloc(ctx, f, b):
     _check(load().igapw_rhs_source_noalloc(ctx, _dptr(f), _dptr(b)), ctx)
 
 
+def igapw_rhs_neumann(ctx, axis, side, g, b):
+    _check(load().igapw_rhs_neumann(ctx, int(axis), int(side), _dptr(g), _dptr(b)), ctx)
+
+
 def igapw_apply(ctx, op, dt, u, r):
     _check(load().igapw_apply(ctx, op, float(dt), _dptr(u), _dptr(r)), ctx)
 
@@ -250,7 +256,7 @@ class Context:
     (2, n_z, n_y, n_x)[...] (hi plane, lo plane) for 'fp32r'."""
 
     def __init__(self, dim, n_elem, degree, nq, test='pw', bc='none', precision='fp64', op='heat',
-                 flags=0, stream=None):
+                 flags=0, stream=None, neumann_axes=0):
         import torch
         if isinstance(n_elem, int):
             n_elem = [n_elem] * dim
@@ -261,6 +267,7 @@ class Context:
         d.degree, d.nq = degree, nq
         d.test, d.bc = TESTS[test], BCS[bc]
         d.precision, d.op, d.flags = PRECISIONS[precision], OPS[op], flags
+        d.neumann_axes = neumann_axes
         self.desc = d
         self.dim, self.p, self.precision = dim, degree, precision
         self.stream = stream if stream is not None else torch.cuda.current_stream()
@@ -313,6 +320,11 @@ class Context:
         out = self.empty() if out is None else out
         igapw_rhs_source(self.ctx, f, out)
         return out
+
+    def rhs_neumann(self, axis, side, g, b):
+        """b += the Neumann data term of the end face `side` of `axis` (in place)."""
+        igapw_rhs_neumann(self.ctx, axis, side, g, b)
+        return b
 
     def quad_points(self, axis):
         return igapw_quad_points(self.ctx, axis)

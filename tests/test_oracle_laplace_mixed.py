@@ -113,3 +113,12 @@ def test_neumann_pencil_spectrum_real_nonnegative():
         assert np.sort(lam.real)[0] > -1e-8 * np.max(lam.real)
         assert np.sort(lam.real)[1] > 1.0
         assert np.linalg.cond(V) < 10
+
+
+def test_sparse_assembly_and_solve_match_dense():
+    axes = [systems.Axis(5, 3, 4, 'pw', 'dirichlet0'), systems.Axis(6, 3, 4, 'pw', 'none')]
+    nm = [False, True]
+    K = LM.assemble(axes, nm)
+    assert np.max(np.abs(LM.assemble_sparse(axes, nm).toarray() - K)) == 0.0
+    b = np.random.default_rng(3).standard_normal((9, 8))
+    assert np.max(np.abs(LM.solve(axes, nm, b, sparse=True) - LM.solve(axes, nm, b))) < 1e-10
