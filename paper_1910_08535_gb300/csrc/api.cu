@@ -175,7 +175,8 @@ int build_axis_device(igapw_ctx* c, int a) {
     fa.L32 = m.L32; fa.U32 = m.U32; fa.dinv32 = m.dinv32; fa.G32 = m.G32; fa.H32 = m.H32;
     fa.PhiF32 = m.PhiF32; fa.PhiB32 = m.PhiB32;
     fa.status = c->status;
-    launch_factor(fa, c->stream);
+    // 2D/3D Poisson contexts solve by fast diagonalisation: no banded LU
+    if (!(c->d.op == IGAPW_OP_POISSON && c->dim >= 2)) launch_factor(fa, c->stream);
     CKC(c, cudaGetLastError());
 
     AxisDev& D = c->dev[a];
