@@ -66,6 +66,10 @@ extern "C" {
 /* ---- descriptor enums --------------------------------------------------- */
 #define IGAPW_GALERKIN      0  /* B-spline tests (comparator)                       */
 #define IGAPW_PWCONST       1  /* piece-wise constant tests                         */
+#define IGAPW_REFINED       2  /* refined test space (Sec. 2): test k is the sum of
+                                  the B-splines of the test space refined `refine`
+                                  times whose Greville abscissae lie in PW cell k;
+                                  tends to the PW test as refine grows           */
 
 #define IGAPW_BC_NONE       0  /* all n coefficients free                           */
 #define IGAPW_BC_DIRICHLET0 1  /* first/last coefficient per axis held at 0 (1D; in
@@ -99,7 +103,8 @@ typedef struct igapw_ctx igapw_ctx;
 /* Problem descriptor.  dim in {1,2,3}; n_elem[a] >= 1 elements on axis a
  * (entries beyond dim ignored); degree p in {2,3,4} (C^{p-1}, at least C^1 as
  * the method requires, Sec. 2); nq >= 1 Gauss points per element (Galerkin) or
- * per polynomial piece of a cell (PW); test = IGAPW_GALERKIN | IGAPW_PWCONST;
+ * per polynomial piece of a cell (PW) or per refined element (REFINED);
+ * test = IGAPW_GALERKIN | IGAPW_PWCONST | IGAPW_REFINED;
  * bc = IGAPW_BC_*; precision = IGAPW_FP64 | IGAPW_FP32_REFINE; op = IGAPW_OP_*
  * selects the matrix igapw_solve inverts (POISSON: -Lap u with bc = DIRICHLET0
  * required -- in 1D the banded 1D operator, in 2D/3D the multi-D operator;
@@ -124,6 +129,8 @@ typedef struct {
     int neumann_axes;   /* POISSON, 2D/3D: bit a set = axis a carries Neumann data on both
                            of its end faces instead of zero Dirichlet rows (Sec. 4.3 mixed
                            boundary conditions); at least one axis must stay Dirichlet */
+    int refine;         /* IGAPW_REFINED: parts per element of the test space (2..64);
+                           its quadrature has nq points per refined element */
 } igapw_desc;
 
 /* Builds knots, Gauss rules and PW cells on the host, evaluates the basis by

@@ -90,6 +90,43 @@ def pw_points(t, p, nq, bc):
     return out
 
 
+def refined_knots(t, r):
+    """Open knot vector with every element of t split into r equal parts
+    (Sec. 2: the test space refined over the same trial functions)."""
+    br = bspline.unique_knots(t)
+    pts = [br[0]]
+    for e in range(len(br) - 1):
+        for k in range(1, r + 1):
+            pts.append(br[e] + (br[e + 1] - br[e]) * k / r)
+    p = sum(1 for x in t if x == t[0]) - 1
+    return np.array([br[0]] * p + pts + [br[-1]] * p, dtype=np.float64)
+
+
+def refined_points(t, p, nq, r):
+    """Gauss points of the refined elements: list of (x, w, element) per element."""
+    tr = refined_knots(t, r)
+    br = bspline.unique_knots(tr)
+    out = []
+    for e in range(len(br) - 1):
+        x, w = map_rule(nq, br[e], br[e + 1])
+        out.append((x, w, e))
+    return out
+
+
+def refined_sets(t, p, r, bc):
+    """Index sets J_k of the refined test B-splines summed into test k: the
+    refined functions whose Greville abscissa lies in PW cell k (cells closed on
+    the left, the last one closed on both sides)."""
+    tr = refined_knots(t, r)
+    g = greville(tr, p)
+    c = pw_cells(t, p, bc)
+    sets = []
+    for k in range(len(c) - 1):
+        last = k == len(c) - 2
+        sets.append([m for m in range(len(g)) if c[k] <= g[m] < c[k + 1] or (last and g[m] == c[k + 1])])
+    return sets
+
+
 def flat_points(pieces):
     """Concatenate a piece list into flat arrays (x, w, owner) in increasing x."""
     x = np.concatenate([pc[0] for pc in pieces])

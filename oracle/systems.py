@@ -24,9 +24,10 @@ class Axis:
     n_elem: int
     p: int
     nq: int
-    test: str = 'pw'          # 'pw' or 'galerkin'
+    test: str = 'pw'          # 'pw', 'galerkin' or 'refined'
     bc: str = 'none'          # 'none' or 'dirichlet0'
     knots: np.ndarray = field(default=None)
+    refine: int = 4           # 'refined': elements of the test space per trial element
 
     def __post_init__(self):
         if self.knots is None:
@@ -40,6 +41,8 @@ class Axis:
     def pieces(self):
         if self.test == 'pw':
             return quadrature.pw_points(self.knots, self.p, self.nq, self.bc)
+        if self.test == 'refined':
+            return quadrature.refined_points(self.knots, self.p, self.nq, self.refine)
         return quadrature.galerkin_points(self.knots, self.p, self.nq)
 
     def points(self):
@@ -63,6 +66,10 @@ def test_matrix(ax):
     Galerkin: W[i, q] = w_q B_i(x_q) (Sec. 4.1 standard loop).
     PW:       W[i, q] = w_q if q lies in the cell paired with row i, else 0
               (Sec. 4.1 PW loop: weight times 1.0).
+    Refined: W[i, q] = w_q sum_{m in J_i} B^_m(x_q) with B^ the B-splines of the
+              test space refined r times and J_i the refined functions whose
+              Greville abscissa lies in cell i (Sec. 2: summing rows of the
+              refined-tested system; the limit r -> inf is the PW test).
     Rows that are not unknowns (Dirichlet rows) stay zero: their RHS is 0.
     """
     x, w, owner = ax.points()
@@ -72,6 +79,11 @@ def test_matrix(ax):
     if ax.test == 'galerkin':
         for i in rows:
             W[i, :] = w * bspline.basis(ax.knots, ax.p, i, x, 0)
+    elif ax.test == 'refined':
+        tr = quadrature.refined_knots(ax.knots, ax.refine)
+        sets = quadrature.refined_sets(ax.knots, ax.p, ax.refine, ax.bc)
+        for k, i in enumerate(rows):
+            W[i, :] = w * sum(bspline.basis(tr, ax.p, m, x, 0) for m in sets[k])
     else:
         for k, i in enumerate(rows):
             W[i, :] = np.where(owner == k, w, 0.0)

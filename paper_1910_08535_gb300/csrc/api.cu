@@ -20,7 +20,7 @@ struct AxisMem {
     double *knots = nullptr, *qx = nullptr, *qw = nullptr, *vals = nullptr;
     int *qfirst = nullptr, *fstart = nullptr, *pstart = nullptr, *pcount = nullptr, *is_free = nullptr;
     double *A = nullptr, *C = nullptr, *S = nullptr, *TW = nullptr;
-    double *dleft = nullptr, *dright = nullptr;
+    double *dleft = nullptr, *dright = nullptr, *twr = nullptr;
     float2 *Adf = nullptr, *Cdf = nullptr, *Sdf = nullptr, *TWdf = nullptr;
     double *band = nullptr, *L = nullptr, *U = nullptr, *dinv = nullptr, *G = nullptr, *H = nullptr,
            *PhiF = nullptr, *PhiB = nullptr;
@@ -129,6 +129,12 @@ int build_axis_device(igapw_ctx* c, int a) {
     CKC(c, upload(c, &m.pstart, s.pstart));
     CKC(c, upload(c, &m.pcount, s.pcount));
     CKC(c, upload(c, &m.is_free, s.is_free));
+    if (s.test == 2) {   // refined tests: host table re-laid with the context's point-window stride
+        std::vector<double> twr((size_t)n * WQ, 0.0);
+        for (int i = 0; i < n; ++i)
+            for (int w = 0; w < s.pcount[i]; ++w) twr[(size_t)i * WQ + w] = s.tw_refined[(size_t)i * s.wq + w];
+        CKC(c, upload(c, &m.twr, twr));
+    }
     CKC(c, upload(c, &m.dleft, s.dleft));
     CKC(c, upload(c, &m.dright, s.dright));
     const int neumann = (c->d.neumann_axes >> a) & 1;
@@ -160,7 +166,7 @@ int build_axis_device(igapw_ctx* c, int a) {
     launch_basis_table(m.knots, p, Q, m.qx, m.qfirst, m.vals, c->stream);
     FoldArgs f{};
     f.n = n; f.p = p; f.W = W; f.WQ = WQ; f.test = s.test; f.poisson = (c->d.op == IGAPW_OP_POISSON && c->dim == 1);
-    f.neumann = neumann; f.dleft = m.dleft; f.dright = m.dright;
+    f.neumann = neumann; f.dleft = m.dleft; f.dright = m.dright; f.twr = m.twr;
     f.fstart = m.fstart; f.pstart = m.pstart; f.pcount = m.pcount; f.is_free = m.is_free;
     f.qfirst = m.qfirst; f.qw = m.qw; f.vals = m.vals;
     f.A = m.A; f.C = m.C; f.S = m.S; f.TW = m.TW;
@@ -316,7 +322,14 @@ int valid_desc(const igapw_desc* d, std::string& why) {
         if (d->n_elem[a] < 1) { why = "n_elem must be >= 1"; return 0; }
     if (d->degree < 2 || d->degree > IGAPW_MAX_DEGREE) { why = "degree must be 2..4 (C^1 or smoother)"; return 0; }
     if (d->nq < 1 || d->nq > 16) { why = "nq must be 1..16"; return 0; }
-    if (d->test != IGAPW_GALERKIN && d->test != IGAPW_PWCONST) { why = "unknown test"; return 0; }
+    if (d->test != IGAPW_GALERKIN && d->test != IGAPW_PWCONST && d->test != IGAPW_REFINED) {
+        why = "unknown test";
+        return 0;
+    }
+    if (d->test == IGAPW_REFINED && (d->refine < 2 || d->refine > 64)) {
+        why = "the refined test space needs refine in 2..64";
+        return 0;
+    }
     if (d->bc != IGAPW_BC_NONE && d->bc != IGAPW_BC_DIRICHLET0) { why = "unknown bc"; return 0; }
     if (d->bc == IGAPW_BC_DIRICHLET0 && d->dim != 1 && d->op != IGAPW_OP_POISSON) {
         why = "Dirichlet rows in 2D/3D are supported for the POISSON system only";
@@ -395,7 +408,7 @@ int setup_all(igapw_ctx* c, const std::vector<double>* knots_override, int overr
         std::vector<double> kn;
         if (knots_override && a == override_axis) kn = *knots_override;
         else if (!c->ax[a].knots.empty() && c->ax[a].n_elem == d.n_elem[a] && knots_override) kn = c->ax[a].knots;
-        std::string e = build_axis(c->ax[a], d.n_elem[a], d.degree, d.nq, d.test, axis_bc(d, a), kn);
+        std::string e = build_axis(c->ax[a], d.n_elem[a], d.degree, d.nq, d.test, axis_bc(d, a), kn, d.refine);
         if (!e.empty()) return fail(c, IGAPW_ERR_ARG, "axis " + std::to_string(a) + ": " + e);
         wmax = std::max(wmax, c->ax[a].w);
         wqmax = std::max(wqmax, c->ax[a].wq);
@@ -473,7 +486,8 @@ int igapw_set_knots(igapw_ctx* c, int axis, const double* knots, int len) {
     CKC(c, cudaStreamSynchronize(c->stream));
     std::vector<double> kn(knots, knots + len);
     AxisSetup trial;
-    std::string e = build_axis(trial, c->d.n_elem[axis], c->d.degree, c->d.nq, c->d.test, axis_bc(c->d, axis), kn);
+    std::string e = build_axis(trial, c->d.n_elem[axis], c->d.degree, c->d.nq, c->d.test, axis_bc(c->d, axis), kn,
+                               c->d.refine);
     if (!e.empty()) return fail(c, IGAPW_ERR_ARG, e);
     // rebuild every axis (the padded window width is shared); keep other axes' knots
     std::vector<std::vector<double>> keep(3);
@@ -485,7 +499,8 @@ int igapw_set_knots(igapw_ctx* c, int axis, const double* knots, int len) {
     CKC(c, cudaMemsetAsync(c->status, 0, sizeof(unsigned), c->stream));
     int wmax = 0, wqmax = 0;
     for (int a = 0; a < c->dim; ++a) {
-        std::string err = build_axis(c->ax[a], c->d.n_elem[a], c->d.degree, c->d.nq, c->d.test, axis_bc(c->d, a), keep[a]);
+        std::string err = build_axis(c->ax[a], c->d.n_elem[a], c->d.degree, c->d.nq, c->d.test, axis_bc(c->d, a), keep[a],
+                                     c->d.refine);
         if (!err.empty()) return fail(c, IGAPW_ERR_ARG, err);
         wmax = std::max(wmax, c->ax[a].w);
         wqmax = std::max(wqmax, c->ax[a].wq);

@@ -17,6 +17,7 @@ struct FoldArgs {
     int neumann;                 // add the Neumann boundary term to C (rows 0 and n-1)
     const double* dleft;         // [n] B_j'(a)
     const double* dright;        // [n] B_j'(b)
+    const double* twr;           // refined test space: w_q T_i(x_q), [n][WQ] (test == 2)
     const int* fstart;
     const int* pstart;
     const int* pcount;

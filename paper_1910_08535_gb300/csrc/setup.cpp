@@ -99,12 +99,13 @@ static void end_derivs(const AxisSetup& ax, int s, double x, std::vector<double>
 }
 
 std::string build_axis(AxisSetup& ax, int n_elem, int p, int nq, int test, int bc,
-                       const std::vector<double>& knots_in) {
+                       const std::vector<double>& knots_in, int refine) {
     ax = AxisSetup();
     if (p < 2 || p > 4) return fmt("degree %d unsupported (2..4: C^1 or smoother)", p);
     if (n_elem < 1) return fmt("n_elem %d < 1", n_elem);
     if (nq < 1 || nq > 16) return fmt("nq %d out of range 1..16", nq);
-    if (test != 0 && test != 1) return fmt("test %d unknown", test);
+    if (test != 0 && test != 1 && test != 2) return fmt("test %d unknown", test);
+    if (test == 2 && (refine < 2 || refine > 64)) return fmt("refine %d out of range 2..64", refine);
     if (bc != 0 && bc != 1) return fmt("bc %d unknown", bc);
     ax.n_elem = n_elem; ax.p = p; ax.nq = nq; ax.test = test; ax.bc = bc;
     ax.n = n_elem + p;
@@ -178,8 +179,9 @@ std::string build_axis(AxisSetup& ax, int n_elem, int p, int nq, int test, int b
 
     ax.pstart.assign(n, 0);
     ax.pcount.assign(n, 0);
-    if (test == 1) {
-        // ---- PW cells: midpoints of consecutive Greville abscissae --------
+    // PW cells (also the groups of the refined test space): midpoints of
+    // consecutive Greville abscissae of the unknowns, domain ends outside
+    auto make_cells = [&]() -> std::string {
         std::vector<double> xi(n);
         for (int j = 0; j < n; ++j) {
             double s = 0.0;
@@ -196,6 +198,11 @@ std::string build_axis(AxisSetup& ax, int n_elem, int p, int nq, int test, int b
         ax.cells.push_back(b);
         for (size_t k = 0; k + 1 < ax.cells.size(); ++k)
             if (!(ax.cells[k + 1] > ax.cells[k])) return "degenerate PW cell";
+        return "";
+    };
+    if (test == 1) {
+        std::string err = make_cells();
+        if (!err.empty()) return err;
         for (size_t k = 0; k < unk.size(); ++k) {
             int row = unk[k];
             double lo = ax.cells[k], hi = ax.cells[k + 1];
@@ -207,6 +214,58 @@ std::string build_axis(AxisSetup& ax, int n_elem, int p, int nq, int test, int b
             add_piece(cur, hi, row);
             ax.pcount[row] = (int)ax.qx.size() - ax.pstart[row];
         }
+    } else if (test == 2) {
+        // ---- refined test space (Sec. 2): every element split into `refine`
+        // parts; test k = sum of the refined B-splines whose Greville abscissa
+        // lies in PW cell k (a contiguous range J_k = [mlo, mhi])
+        std::string err = make_cells();
+        if (!err.empty()) return err;
+        std::vector<double> tr(p, a);
+        for (int e = 0; e < ne; ++e)
+            for (int k = 0; k < refine; ++k) tr.push_back(ax.brk[e] + (ax.brk[e + 1] - ax.brk[e]) * k / refine);
+        for (int k = 0; k <= p; ++k) tr.push_back(b);
+        const int nr = (int)tr.size() - p - 1;     // refined functions
+        const int ner = ne * refine;               // refined elements
+        std::vector<int> mlo(unk.size(), nr), mhi(unk.size(), -1);
+        for (int m = 0; m < nr; ++m) {
+            double g = 0.0;
+            for (int k = m + 1; k <= m + p; ++k) g += tr[k];
+            g /= p;
+            size_t k = 0;
+            while (k + 1 < unk.size() && !(g < ax.cells[k + 1])) ++k;   // cell k: [c_k, c_{k+1}), last closed
+            mlo[k] = std::min(mlo[k], m);
+            mhi[k] = std::max(mhi[k], m);
+        }
+        std::vector<int> er_first_pt(ner);
+        for (int er = 0; er < ner; ++er) {
+            er_first_pt[er] = (int)ax.qx.size();
+            add_piece(tr[p + er], tr[p + er + 1], -1);
+        }
+        // test values at the points of each row's support
+        std::vector<std::vector<double>> rowvals(n);
+        for (size_t k = 0; k < unk.size(); ++k) {
+            const int row = unk[k];
+            if (mhi[k] < mlo[k]) return "refined test without functions (refine too small)";
+            const int e0 = std::max(0, mlo[k] - p), e1 = std::min(ner - 1, mhi[k]);
+            ax.pstart[row] = er_first_pt[e0];
+            ax.pcount[row] = (e1 - e0 + 1) * nq;
+            for (int er = e0; er <= e1; ++er) {
+                for (int q = 0; q < nq; ++q) {
+                    const int pt = er_first_pt[er] + q;
+                    double N[8];
+                    span_values(tr, p + er, p, ax.qx[pt], N);
+                    double t = 0.0;
+                    for (int r = 0; r <= p; ++r)
+                        if (er + r >= mlo[k] && er + r <= mhi[k]) t += N[r];
+                    rowvals[row].push_back(ax.qw[pt] * t);
+                }
+            }
+        }
+        int wq = 0;
+        for (int i = 0; i < n; ++i) wq = std::max(wq, ax.pcount[i]);
+        ax.tw_refined.assign((size_t)n * std::max(wq, 1), 0.0);
+        for (int i = 0; i < n; ++i)
+            for (size_t c = 0; c < rowvals[i].size(); ++c) ax.tw_refined[(size_t)i * wq + c] = rowvals[i][c];
     } else {
         // ---- Galerkin: nq Gauss points per element -------------------------
         std::vector<int> efirst_pt(ne);

@@ -42,6 +42,10 @@ struct AxisSetup {
     // PW cell break points (empty for Galerkin)
     std::vector<double> cells;
 
+    // refined test space: w_q T_i(x_q) over each row's point window, [n][wq]
+    // (rows of width wq; B-spline and PW tests compute theirs on the device)
+    std::vector<double> tw_refined;
+
     // first derivatives of every basis function at the two ends of the axis
     // (the Neumann boundary term of Sec. 4.3 uses them)
     std::vector<double> dleft, dright;
@@ -49,8 +53,10 @@ struct AxisSetup {
 
 // Builds everything for one axis from (n_elem, p, nq, test, bc) and optional
 // caller knots (empty = open uniform on [0,1]).  Returns "" or an error text.
+// test: 0 B-splines, 1 PW cells, 2 refined test space (`refine` parts per
+// element, Sec. 2).
 std::string build_axis(AxisSetup& ax, int n_elem, int p, int nq, int test, int bc,
-                       const std::vector<double>& knots_in);
+                       const std::vector<double>& knots_in, int refine = 0);
 
 // Re-centres the function windows for a padded kernel width wk >= ax.w:
 // fstart[i] = max(0, min(flo[i], n - wk)).  False if the starts do not step by

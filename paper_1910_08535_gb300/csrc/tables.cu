@@ -104,6 +104,8 @@ __global__ void fold_kernel(FoldArgs f) {
                 if (f.test == 0) {
                     const int ai = i - first;
                     tw *= (ai >= 0 && ai <= f.p) ? f.vals[((size_t)q * (f.p + 1) + ai) * 3] : 0.0;
+                } else if (f.test == 2) {
+                    tw = f.twr[(size_t)i * f.WQ + (q - q0)];
                 }
                 sa += tw * f.vals[((size_t)q * (f.p + 1) + a) * 3 + 0];
                 sc += tw * f.vals[((size_t)q * (f.p + 1) + a) * 3 + 2];
@@ -138,6 +140,8 @@ __global__ void fold_kernel(FoldArgs f) {
             if (f.test == 0) {
                 const int ai = i - f.qfirst[q];
                 tw *= (ai >= 0 && ai <= f.p) ? f.vals[((size_t)q * (f.p + 1) + ai) * 3] : 0.0;
+            } else if (f.test == 2) {
+                tw = f.twr[(size_t)i * f.WQ + w];
             }
         }
         f.TW[k] = tw;

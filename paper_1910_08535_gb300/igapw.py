@@ -17,13 +17,13 @@ HEADER = os.path.join(os.path.dirname(HERE), 'include', 'igapw.h')
 # constants mirrored from include/igapw.h (checked against it by the tests)
 IGAPW_OK, IGAPW_ERR_ARG, IGAPW_ERR_SINGULAR, IGAPW_ERR_OOM = 0, -1, -2, -3
 IGAPW_ERR_CUDA, IGAPW_ERR_DEVICE_STATUS, IGAPW_ERR_TIMEOUT = -4, -5, -6
-IGAPW_GALERKIN, IGAPW_PWCONST = 0, 1
+IGAPW_GALERKIN, IGAPW_PWCONST, IGAPW_REFINED = 0, 1, 2
 IGAPW_BC_NONE, IGAPW_BC_DIRICHLET0 = 0, 1
 IGAPW_FP64, IGAPW_FP32_REFINE = 0, 1
 IGAPW_OP_MASS, IGAPW_OP_LAPLACE, IGAPW_OP_HEAT, IGAPW_OP_POISSON = 0, 1, 2, 3
 IGAPW_FLAG_FP64_RESIDUAL, IGAPW_FLAG_STEP_RHS_SOLVE, IGAPW_FLAG_FDM_BF16X9 = 1, 2, 4
 
-TESTS = {'galerkin': IGAPW_GALERKIN, 'pw': IGAPW_PWCONST}
+TESTS = {'galerkin': IGAPW_GALERKIN, 'pw': IGAPW_PWCONST, 'refined': IGAPW_REFINED}
 BCS = {'none': IGAPW_BC_NONE, 'dirichlet0': IGAPW_BC_DIRICHLET0}
 PRECISIONS = {'fp64': IGAPW_FP64, 'fp32r': IGAPW_FP32_REFINE}
 OPS = {'mass': IGAPW_OP_MASS, 'laplace': IGAPW_OP_LAPLACE, 'heat': IGAPW_OP_HEAT, 'poisson': IGAPW_OP_POISSON}
@@ -39,7 +39,7 @@ class igapw_desc(ctypes.Structure):
     _fields_ = [('dim', ctypes.c_int), ('n_elem', ctypes.c_int * 3), ('degree', ctypes.c_int),
                 ('nq', ctypes.c_int), ('test', ctypes.c_int), ('bc', ctypes.c_int),
                 ('precision', ctypes.c_int), ('op', ctypes.c_int), ('flags', ctypes.c_int),
-                ('neumann_axes', ctypes.c_int)]
+                ('neumann_axes', ctypes.c_int), ('refine', ctypes.c_int)]
 
 
 _VP, _I, _D = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
@@ -256,7 +256,7 @@ class Context:
     (2, n_z, n_y, n_x)[...] (hi plane, lo plane) for 'fp32r'."""
 
     def __init__(self, dim, n_elem, degree, nq, test='pw', bc='none', precision='fp64', op='heat',
-                 flags=0, stream=None, neumann_axes=0):
+                 flags=0, stream=None, neumann_axes=0, refine=0):
         import torch
         if isinstance(n_elem, int):
             n_elem = [n_elem] * dim
@@ -268,6 +268,7 @@ class Context:
         d.test, d.bc = TESTS[test], BCS[bc]
         d.precision, d.op, d.flags = PRECISIONS[precision], OPS[op], flags
         d.neumann_axes = neumann_axes
+        d.refine = refine
         self.desc = d
         self.dim, self.p, self.precision = dim, degree, precision
         self.stream = stream if stream is not None else torch.cuda.current_stream()

@@ -5,10 +5,10 @@ import numpy as np
 from oracle import systems
 
 
-def oracle_axes(dim, n_elem, p, nq, test, bc='none'):
+def oracle_axes(dim, n_elem, p, nq, test, bc='none', refine=4):
     if isinstance(n_elem, int):
         n_elem = [n_elem] * dim
-    return [systems.Axis(n_elem[a], p, nq, test, bc) for a in range(dim)]
+    return [systems.Axis(n_elem[a], p, nq, test, bc, refine=refine) for a in range(dim)]
 
 
 def rel_l2(a, b):

@@ -33,14 +33,14 @@ def test_constants_match_header():
 
 
 def test_desc_layout_matches_header():
-    """igapw_desc is ten fields (twelve ints) in the header's order."""
+    """igapw_desc is eleven fields (thirteen ints) in the header's order."""
     from paper_1910_08535_gb300 import igapw
     txt = open(igapw.HEADER).read()
     body = re.search(r'typedef struct \{(.*?)\} igapw_desc;', txt, re.S).group(1)
     fields = re.findall(r'int\s+(\w+)(?:\[(\d)\])?;', body)
     assert [f[0] for f in fields] == [f[0] for f in igapw.igapw_desc._fields_]
     import ctypes
-    assert ctypes.sizeof(igapw.igapw_desc) == 12 * 4
+    assert ctypes.sizeof(igapw.igapw_desc) == 13 * 4
 
 
 def test_missing_library_fails_loudly(tmp_path):
