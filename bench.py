@@ -329,6 +329,7 @@ def measure_serving(requests=2000, seed=6, budget=120 * 10 ** 9):
     300 requests, then `requests` Poisson arrivals at 80% of that capacity."""
     import torch
     from paper_1910_08535_gb300 import serve
+    torch.cuda.empty_cache()        # the rows before leave cached blocks of other sizes
     srv = serve.Server(budget_bytes=budget)
     stream = serve.make_stream(requests, rate=1.0, seed=seed)
     probe = serve.make_stream(300, rate=None, seed=seed + 1)

@@ -238,11 +238,17 @@ class Server:
         self.created += 1
         return s
 
-    def warm(self, shapes):
-        """Create (and park) one slot per shape ahead of a stream."""
+    def warm(self, shapes, steps=20, dt_h2=0.05):
+        """Create (and park) one slot per shape ahead of a stream, each running
+        one dry request of the stream's kind (so that its step graph is captured
+        and its buffers are allocated before the first real request)."""
         for sh in shapes:
-            if not self.pools[sh] and self.used + slot_bytes(sh) <= self.budget:
-                self.pools[sh].append(self.acquire(sh))
+            if not self.pools[sh] and self.used + slot_bytes(sh) + transient_bytes(sh) <= self.budget:
+                slot = self.acquire(sh)
+                slot.launch(Request(-1, 0.0, sh, steps=steps, dt_h2=dt_h2, k=(1,) * sh.dim))
+                slot.done.synchronize()
+                slot.retire()
+                self.pools[sh].append(slot)
 
     def run(self, requests, keep_results=False, clock=time.perf_counter):
         """Serve `requests`; returns (records by rid, results by rid)."""
