@@ -68,8 +68,13 @@ __device__ __forceinline__ void st_state(void* p, long long g, long long, double
 
 // MODE: 0 FIRST (acc = u + dt w), 1 MID (acc += dt w), 2 LAST (u = acc + dt w),
 // 3 ONLY (u = u + dt w).  XL: lines along x (contiguous) or along y/z.
-template <typename VT, int KP, int W, int MODE, bool XL, bool TG>
+// CFG: 0 = tables staged, 32 columns per y/z block (or x-lines); 1 = tables
+// read from global memory (long lines), runtime lines/columns; 2 = tables
+// staged, 16 columns per y/z block (less shared memory per block: more
+// resident blocks per SM).
+template <typename VT, int KP, int W, int MODE, bool XL, int CFG>
 __global__ void __launch_bounds__(256) axis_step_kernel(const AxisStepArgs a) {
+    constexpr bool TG = (CFG == 1);
     using TS = typename StepTypes<VT>::S;
     constexpr bool DFM = std::is_same<VT, DF>::value;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -128,7 +133,7 @@ __global__ void __launch_bounds__(256) axis_step_kernel(const AxisStepArgs a) {
     const int nr = n + W;
     // staged y/z blocks always hold 32 columns: a compile-time pitch of 33 turns
     // the row offsets of the banded windows into immediate offsets
-    const int pitch = XL ? (nr | 1) : (TG ? NL + 1 : 33);
+    const int pitch = XL ? (nr | 1) : (TG ? NL + 1 : (CFG == 2 ? 17 : 33));
     const int st = XL ? 1 : pitch;      // row stride within a line
     const int lst = XL ? pitch : 1;     // line stride
     const int cap = XL ? NL * pitch : nr * pitch;
@@ -144,11 +149,11 @@ __global__ void __launch_bounds__(256) axis_step_kernel(const AxisStepArgs a) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     // y/z-lines: lane -> column cl of the block's NL columns, row offset ro of
     // the RPW rows a warp covers per pass
-    // (staged tables always come with all 32 columns: lane = column)
-    const int lgNL = (XL || !TG) ? 0 : __ffs(NL) - 1;
-    const int cl = XL ? 0 : (TG ? (lane & (NL - 1)) : lane);
-    const int ro = (XL || !TG) ? 0 : (lane >> lgNL);
-    const int RPW = (XL || !TG) ? 1 : (32 >> lgNL);
+    // (staged tables come with 32 or 16 columns, fixed at compile time)
+    const int lgNL = (XL || CFG == 0) ? 0 : (CFG == 2 ? 4 : __ffs(NL) - 1);
+    const int cl = XL ? 0 : (CFG == 0 ? lane : (lane & ((1 << lgNL) - 1)));
+    const int ro = (XL || CFG == 0) ? 0 : (lane >> lgNL);
+    const int RPW = (XL || CFG == 0) ? 1 : (32 >> lgNL);
     long long l0 = 0, os = 0, rs = 0;
     int nl, x0 = 0;
     if (XL) {
@@ -364,20 +369,39 @@ static cudaError_t run_axis_step(const AxisStepArgs& a0, cudaStream_t st) {
     // lines (a power of two for columns) as fit.
     const int nl_max = xl ? (int)std::min<long long>(32, nlines) : 32;
     int NL = nl_max;
-    bool tg = false;
+    int cfg = 0;
     while (xl && NL > 8 && smem_for(NL, false) > (size_t)lim) NL = (NL + 1) / 2;
     if (smem_for(NL, false) > (size_t)lim) {
-        tg = true;
+        cfg = 1;
         NL = nl_max;
         while (NL > 1 && smem_for(NL, true) > (size_t)lim) NL = xl ? (NL + 1) / 2 : NL / 2;
     }
+    if (!xl && cfg == 0) {
+        // 16 staged columns when that keeps more blocks resident per SM (the
+        // step is latency-bound: 3 blocks of 16 columns beat 2 of 32 on 131-row
+        // lines, 174 vs 190 us per heat3d step; 8 columns lose again)
+        int smsm = 0;
+        cudaDeviceGetAttribute(&smsm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+        auto resident = [&](size_t b) { return std::min<long long>(8, (long long)smsm / (long long)(b + 1024)); };
+        if (resident(smem_for(16, false)) > resident(smem_for(32, false))) {
+            cfg = 2;
+            NL = 16;
+        }
+    }
     a.lines_per_block = NL;
-    const size_t sm = smem_for(NL, tg);
+    const size_t sm = smem_for(NL, cfg == 1);
     if (sm > (size_t)lim) return cudaErrorInvalidValue;
     // modes 0 (first of several axes) and 3 (1D) run along x, modes 1 and 2 across
     constexpr bool XL = (MODE == 0 || MODE == 3);
     if (xl != XL) return cudaErrorInvalidValue;
-    auto k = tg ? axis_step_kernel<VT, KP, W, MODE, XL, true> : axis_step_kernel<VT, KP, W, MODE, XL, false>;
+    void (*k)(const AxisStepArgs) = nullptr;
+    if constexpr (XL) {
+        k = cfg == 1 ? axis_step_kernel<VT, KP, W, MODE, XL, 1> : axis_step_kernel<VT, KP, W, MODE, XL, 0>;
+    } else {
+        k = cfg == 1   ? axis_step_kernel<VT, KP, W, MODE, XL, 1>
+            : cfg == 2 ? axis_step_kernel<VT, KP, W, MODE, XL, 2>
+                       : axis_step_kernel<VT, KP, W, MODE, XL, 0>;
+    }
     if (sm > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if constexpr (XL) {
         k<<<(unsigned)((nlines + NL - 1) / NL), 256, sm, st>>>(a);
