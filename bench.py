@@ -382,6 +382,31 @@ def measure_batch(stream, count=512, seed=0, reps=10):
     return out
 
 
+def measure_ladder(stream, flush, hbm_peak, sizes=((256, 3), (384, 3), (256, 2), (192, 4)), reps=5):
+    """Row a9 (size ladder past L2): one explicit step of the 3D heat problem
+    (PW, FP32 pairs, 1e-2 N(0,1) coefficients, dt = 0.05 h^2) at grids whose
+    state (8 bytes per DOF as pairs) exceeds the 129 MB L2; L2 flushed before
+    each step.  Reports DOF-updates/s and the step's algorithmic HBM rate
+    (read u, write u': 16 bytes per DOF)."""
+    import torch
+    from paper_1910_08535_gb300 import workloads
+    from paper_1910_08535_gb300.igapw import Context
+    out = []
+    for ne, p in sizes:
+        with torch.cuda.stream(stream):
+            c = Context(dim=3, n_elem=ne, degree=p, nq=p + 1, test='pw', precision='fp32r', stream=stream)
+            u = c.from_numpy(workloads.normal_coeffs(c.shape, seed=ne))
+            dt = 0.05 / ne ** 2
+            t = _time_events(stream, lambda: c.step(u, dt, 1), reps, flush)
+            c.sync()
+        out.append({'n_elem': ne, 'degree': p, 'dof': c.ntot, 'state_mb': 8 * c.ntot / 1e6, 'step_us': t * 1e6,
+                    'dof_updates_per_s': c.ntot / t, 'alg_hbm_gbs': 16 * c.ntot / t / 1e9,
+                    'alg_hbm_frac': 16 * c.ntot / t / 1e9 / hbm_peak})
+        c.close()
+        del u
+    return out
+
+
 def cpu_baseline_batch(res, sample=8):
     """Oracle side of row a8: sampled instances' solutions against the oracle
     (backward error) and the oracle's sparse direct solve timed per instance."""
@@ -544,6 +569,7 @@ def run_native(args, rank, world):
     poisson = measure_poisson(stream, flush)
     rows['a7_poisson_2d_1024'] = cpu_baseline_poisson(poisson)
     rows['a8_batch_poisson_512'] = cpu_baseline_batch(measure_batch(stream))
+    rows['a9_size_ladder'] = measure_ladder(stream, flush, hbm_peak)
     # the request server is a one-GPU process: measured at N = 1
     serving = measure_serving() if (world == 1 and not args.no_serve) else None
 
