@@ -61,6 +61,9 @@ struct igapw_ctx {
     std::string err;
     std::vector<GraphEntry> graphs;
     FdmState* fdm = nullptr;  // multi-D Poisson contexts: spectral data of the 1D pencils
+    // split-step launch shapes per axis picked by timing (-1: not tuned yet)
+    int step_cfg[3] = {-1, -1, -1};
+    int step_nl[3] = {0, 0, 0};
 };
 
 namespace {
@@ -299,6 +302,8 @@ int enqueue_steps(igapw_ctx* c, double dt, int nsteps, void* u, cudaStream_t st)
                 a.acc = c->r;
                 a.dt = dt;
                 a.status = c->status;
+                a.cfg = c->step_cfg[ax];
+                a.lines_per_block = c->step_nl[ax];
                 const int mode = c->dim == 1 ? 3 : (ax == 0 ? 0 : (ax == c->dim - 1 ? 2 : 1));
                 cudaError_t e = launch_axis_step(a, mode, fp64(c), c->p, st);
                 if (e != cudaSuccess) return fail(c, IGAPW_ERR_CUDA, std::string("axis step: ") + cudaGetErrorString(e));
@@ -313,6 +318,67 @@ int enqueue_steps(igapw_ctx* c, double dt, int nsteps, void* u, cudaStream_t st)
         if (rc) return rc;
     }
     return IGAPW_OK;
+}
+
+// Split-step autotuner: per axis, times every launch shape of the step kernel
+// (staged tables with 32 / 16 lines or columns, tables in global memory with
+// 32 / 16 / 8) on zeroed scratch tensors and keeps the fastest.  Runs once per
+// context, before the first step is captured.
+int tune_step(igapw_ctx* c, double dt) {
+    static const int cand[][2] = {{0, 32}, {0, 16}, {0, 8}, {2, 16}, {1, 32}, {1, 16}, {1, 8}};
+    const size_t bytes = (size_t)c->ntot * 8;   // one pair or FP64 tensor
+    unsigned char *tu = nullptr, *tacc = nullptr;
+    CKC(c, cudaMallocAsync((void**)&tu, bytes, c->stream));
+    CKC(c, cudaMallocAsync((void**)&tacc, bytes, c->stream));
+    CKC(c, cudaMemsetAsync(tu, 0, bytes, c->stream));
+    CKC(c, cudaMemsetAsync(tacc, 0, bytes, c->stream));
+    cudaEvent_t e0, e1;
+    CKC(c, cudaEventCreate(&e0));
+    CKC(c, cudaEventCreate(&e1));
+    int rc = IGAPW_OK;
+    for (int ax = 0; ax < c->dim && !rc; ++ax) {
+        const int mode = c->dim == 1 ? 3 : (ax == 0 ? 0 : (ax == c->dim - 1 ? 2 : 1));
+        float best = 1e30f;
+        for (const auto& cd : cand) {
+            AxisStepArgs a{};
+            a.axis = ax;
+            for (int k = 0; k < 3; ++k) a.n[k] = c->n[k];
+            a.W = c->W;
+            a.ntot = c->ntot;
+            a.ax = c->dev[ax];
+            a.u = tu;
+            a.u_out = tu;
+            a.acc = tacc;
+            a.dt = dt;
+            a.status = c->status;
+            a.cfg = cd[0];
+            a.lines_per_block = cd[1];
+            if (launch_axis_step(a, mode, fp64(c), c->p, c->stream) != cudaSuccess) {
+                cudaGetLastError();   // shape not valid for this axis: skip
+                continue;
+            }
+            cudaEventRecord(e0, c->stream);
+            for (int r = 0; r < 3; ++r) launch_axis_step(a, mode, fp64(c), c->p, c->stream);
+            cudaEventRecord(e1, c->stream);
+            if (cudaEventSynchronize(e1) != cudaSuccess) {
+                rc = fail(c, IGAPW_ERR_CUDA, "step autotuning failed");
+                break;
+            }
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < best) {
+                best = ms;
+                c->step_cfg[ax] = cd[0];
+                c->step_nl[ax] = cd[1];
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFreeAsync(tu, c->stream);
+    cudaFreeAsync(tacc, c->stream);
+    CKC(c, cudaStreamSynchronize(c->stream));
+    return rc;
 }
 
 int valid_desc(const igapw_desc* d, std::string& why) {
@@ -495,6 +561,7 @@ int igapw_set_knots(igapw_ctx* c, int axis, const double* knots, int len) {
     keep[axis] = kn;
     free_graphs(c);
     release(c);
+    for (int a = 0; a < 3; ++a) c->step_cfg[a] = -1;   // launch shapes are re-tuned
     CKC(c, dalloc(c, &c->status, 1));
     CKC(c, cudaMemsetAsync(c->status, 0, sizeof(unsigned), c->stream));
     int wmax = 0, wqmax = 0;
@@ -672,6 +739,10 @@ int igapw_step(igapw_ctx* c, double dt, int nsteps, void* u_dev) {
     if (!u_dev || nsteps < 0) return fail(c, IGAPW_ERR_ARG, "bad arguments");
     if (c->d.op == IGAPW_OP_POISSON) return fail(c, IGAPW_ERR_ARG, "explicit steps need a mass-matrix context (op != POISSON)");
     if (nsteps == 0) return IGAPW_OK;
+    if (!(c->d.flags & IGAPW_FLAG_STEP_RHS_SOLVE) && c->step_cfg[0] < 0) {
+        const int rc = tune_step(c, dt);
+        if (rc) return rc;
+    }
     // graphs of up to CHUNK steps, replayed
     const int CHUNK = 50;
     int left = nsteps;

@@ -129,7 +129,9 @@ struct AxisStepArgs {
     int n[3];
     int W;
     int lines_per_block;    // lines staged per block: x-lines, or columns (a power of
-                            // two <= 32) of y/z-lines (set by the launcher)
+                            // two <= 32) of y/z-lines (set by the launcher, or forced)
+    int cfg;                // -1: the launcher's own choice; else forced with lines_per_block:
+                            // 0 staged tables, 1 tables in global memory, 2 staged 16 columns
     long long ntot;
     AxisDev ax;
     const void* u;

@@ -319,16 +319,16 @@ std::string build_axis(AxisSetup& ax, int n_elem, int p, int nq, int test, int b
 }
 
 void set_chunks(AxisSetup& ax, long long lines) {
-    // P a power of two <= 32 (the lane group of a warp that shares a line).
-    // With many lines (>= 65536) every lane solves a whole line (P = 1): no
-    // scans or spike corrections, and still >= 256 warps of independent
-    // recurrences.  Otherwise the smallest P whose chunks fit the
-    // register-resident solve (ceil(n / P) <= 20 rows), never with chunks
-    // shorter than p rows.
+    // P a power of two <= 32 (the lane group of a warp that shares a line):
+    // the smallest P whose chunks fit the register-resident solve
+    // (ceil(n / P) <= 20 rows), never with chunks shorter than p rows.  The
+    // split step solves the few lines a block holds, so one lane per whole line
+    // (P = 1) would leave most of its threads idle in the solve phases however
+    // many lines the batch has (`lines` is kept for the interface).
+    (void)lines;
     const int n = ax.n, p = ax.p;
     ax.P = 1;
-    if (lines < 65536)
-        while (ax.P < 32 && (n + ax.P - 1) / ax.P > 20 && n / (2 * ax.P) >= p) ax.P *= 2;
+    while (ax.P < 32 && (n + ax.P - 1) / ax.P > 20 && n / (2 * ax.P) >= p) ax.P *= 2;
     for (int k = 0; k <= ax.P; ++k) ax.chunk_b[k] = (int)((long long)k * n / ax.P);
 }
 

@@ -388,6 +388,13 @@ static cudaError_t run_axis_step(const AxisStepArgs& a0, cudaStream_t st) {
             NL = 16;
         }
     }
+    if (a0.cfg >= 0) {   // forced (autotuner): validate the shape
+        cfg = a0.cfg;
+        NL = cfg == 2 ? 16 : a0.lines_per_block;
+        if (NL < 1 || NL > nl_max || (cfg == 2 && xl) || cfg > 2) return cudaErrorInvalidValue;
+        if (!xl && (NL & (NL - 1))) return cudaErrorInvalidValue;
+        if (!xl && cfg == 0 && NL != 32) return cudaErrorInvalidValue;
+    }
     a.lines_per_block = NL;
     const size_t sm = smem_for(NL, cfg == 1);
     if (sm > (size_t)lim) return cudaErrorInvalidValue;
