@@ -539,8 +539,13 @@ def run_native(args, rank, world):
     sm_mhz = pk.get('sm_max_mhz', 2070.0)
     alu_peak = 152 * 128 * sm_mhz * 1e6 / 1e12
     achieved = alg_ops / t_one / 1e12
+    # DRAM bytes of one step (3 launches, x staged 32 lines, y/z staged 16 columns) from
+    # one ncu capture of `python -m paper_1910_08535_gb300.profile_cases heat3d-step`
+    # (dram__bytes_read.sum + dram__bytes_write.sum, cold-cache replay)
+    step_traffic = 90.3e6
     roof = {'bound': 'alu', 'achieved': achieved, 'peak': alu_peak, 'unit': 'TFLOP/s', 'frac': achieved / alu_peak,
-            'traffic': None, 'kernel': 'axis_step_kernel<DF,3,5,*> x3 (one explicit step, PW)',
+            'traffic': step_traffic, 'traffic_note': 'bytes per step (3 launches), ncu cold-cache replay',
+            'kernel': 'axis_step_kernel<DF,3,5,*> x3 (one explicit step, PW)',
             'peak_kind': f'derived: 152 SMs x 128 FP32 lanes x {sm_mhz:.0f} MHz (FP32 operations/s, FMA = 1)',
             'alg_ops_per_step': alg_ops, 'step_us': t_one * 1e6}
     hbm_peak = pk.get('hbm_gbs', 6800.0)
