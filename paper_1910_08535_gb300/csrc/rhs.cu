@@ -208,6 +208,68 @@ __global__ void __launch_bounds__(256) neumann_face_kernel(const NeumannArgs a) 
     }
 }
 
+// PW source with the x-window of every sample row loaded before it is summed
+// (up to MAXW points per cell and axis, predicated): the loads of a row are in
+// flight together instead of one per dependent compensated product.
+template <typename CT, int IN_F32, int MAXW>
+__global__ void __launch_bounds__(256) source_pw_rows_kernel(const SourceArgs a) {
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int nx = a.n[0], ny = a.n[1], nz = a.n[2];
+    if (e >= (long long)nx * ny * nz) return;
+    const int i = (int)(e % nx);
+    const long long t = e / nx;
+    const int j = (int)(t % ny);
+    const int k = (int)(t / ny);
+    const int Qx = a.q[0], Qy = a.q[1], Qz = a.q[2];
+    const AxisDev& X = a.ax[0];
+    const int wx = X.wq, psx = X.pstart[i];
+    const int wy = a.dim >= 2 ? a.ax[1].wq : 1, psy = a.dim >= 2 ? a.ax[1].pstart[j] : 0;
+    const int wz = a.dim >= 3 ? a.ax[2].wq : 1, psz = a.dim >= 3 ? a.ax[2].pstart[k] : 0;
+    CT tx[MAXW];
+#pragma unroll
+    for (int c = 0; c < MAXW; ++c) tx[c] = c < wx ? tab<CT>(X.TW, i * wx + c) : zero_v<CT>();
+    Acc<CT> acc;
+    acc.init();
+    for (int az = 0; az < wz; ++az) {
+        const int qz = psz + az;
+        if (qz >= Qz) break;
+        const CT tz = a.dim >= 3 ? tab<CT>(a.ax[2].TW, k * wz + az) : from_double<CT>(1.0);
+        for (int by = 0; by < wy; ++by) {
+            const int qy = psy + by;
+            if (qy >= Qy) break;
+            const CT ty = a.dim >= 2 ? tab<CT>(a.ax[1].TW, j * wy + by) : from_double<CT>(1.0);
+            const long long row = ((long long)qz * Qy + qy) * Qx;
+            float fv[MAXW];
+            double dv[MAXW];
+#pragma unroll
+            for (int c = 0; c < MAXW; ++c) {
+                const int qx = psx + c;
+                const bool in = c < wx && qx < Qx;
+                if constexpr (IN_F32) fv[c] = in ? ((const float*)a.f)[row + qx] : 0.f;
+                else dv[c] = in ? ((const double*)a.f)[row + qx] : 0.0;
+            }
+            Acc<CT> sx;
+            sx.init();
+#pragma unroll
+            for (int c = 0; c < MAXW; ++c) {
+                if (c < wx) {
+                    if constexpr (std::is_same<CT, double>::value) sx.add_prod(tx[c], IN_F32 ? (double)fv[c] : dv[c]);
+                    else sx.add_prod_f(tx[c], fv[c]);
+                }
+            }
+            if constexpr (std::is_same<CT, double>::value) acc.add_prod(tz * ty, sx.result());
+            else acc.add_prod(df_mul(tz, ty), sx.result());
+        }
+    }
+    const CT r = acc.result();
+    if constexpr (std::is_same<CT, double>::value) {
+        ((double*)a.out)[e] = r;
+    } else {
+        ((float*)a.out)[e] = r.hi;
+        ((float*)a.out)[e + a.ntot] = r.lo;
+    }
+}
+
 cudaError_t launch_neumann(const NeumannArgs& a, int fp64, cudaStream_t st) {
     long long face = 1;
     for (int k = 0; k < a.dim; ++k)
@@ -222,8 +284,20 @@ cudaError_t launch_source(const SourceArgs& a, int fp64, cudaStream_t st) {
     if (a.pw) {
         const long long total = (long long)a.n[0] * a.n[1] * a.n[2];
         const unsigned blocks = (unsigned)((total + 255) / 256);
-        if (fp64) source_pw_kernel<double, 0><<<blocks, 256, 0, st>>>(a);
-        else source_pw_kernel<DF, 1><<<blocks, 256, 0, st>>>(a);
+        const int wx = a.ax[0].wq;
+        if (wx <= 4) {
+            if (fp64) source_pw_rows_kernel<double, 0, 4><<<blocks, 256, 0, st>>>(a);
+            else source_pw_rows_kernel<DF, 1, 4><<<blocks, 256, 0, st>>>(a);
+        } else if (wx <= 8) {
+            if (fp64) source_pw_rows_kernel<double, 0, 8><<<blocks, 256, 0, st>>>(a);
+            else source_pw_rows_kernel<DF, 1, 8><<<blocks, 256, 0, st>>>(a);
+        } else if (wx <= 16) {
+            if (fp64) source_pw_rows_kernel<double, 0, 16><<<blocks, 256, 0, st>>>(a);
+            else source_pw_rows_kernel<DF, 1, 16><<<blocks, 256, 0, st>>>(a);
+        } else {
+            if (fp64) source_pw_kernel<double, 0><<<blocks, 256, 0, st>>>(a);
+            else source_pw_kernel<DF, 1><<<blocks, 256, 0, st>>>(a);
+        }
         return cudaGetLastError();
     }
     // Galerkin: passes x (Ni = 1), then y (Ni = n_x), then z (Ni = n_x n_y)
