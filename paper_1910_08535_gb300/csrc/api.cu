@@ -190,7 +190,7 @@ int build_axis_device(igapw_ctx* c, int a) {
 
     AxisDev& D = c->dev[a];
     D.n = n; D.nq = Q; D.wq = WQ;
-    D.fstart = m.fstart; D.pstart = m.pstart; D.is_free = m.is_free;
+    D.fstart = m.fstart; D.pstart = m.pstart; D.pcount = m.pcount; D.is_free = m.is_free;
     D.A = {m.A, m.Adf};
     D.C = {m.C, m.Cdf};
     D.S = {m.S, m.Sdf};

@@ -123,6 +123,7 @@ struct AxisDev {
     int wq;         // point-window width (padded)
     const int* fstart;   // [n]
     const int* pstart;   // [n]
+    const int* pcount;   // [n] points of each row's window actually carrying its test
     const int* is_free;  // [n]
     TableSet A;     // int T_i B_j        (Dirichlet rows: identity)
     TableSet C;     // int T_i B_j''      (Dirichlet rows: zero)

@@ -1,5 +1,6 @@
 // Kernel (b): contraction launch dispatch (operator, system and residual
 // modes; the kernel template is in contract.cuh) and the source RHS kernels.
+#include <algorithm>
 #include <type_traits>
 
 #include "contract.cuh"
@@ -208,11 +209,77 @@ __global__ void __launch_bounds__(256) neumann_face_kernel(const NeumannArgs a) 
     }
 }
 
+// PW source, loads batched: for every z point of the cell, the whole y-by-x
+// slab of the cell's samples (its own point counts, at most MAXW per axis) is
+// loaded before it is summed, so a thread keeps up to MAXW^2 loads in flight.
+template <typename CT, int IN_F32, int MAXW>
+__global__ void __launch_bounds__(256) source_pw_rows_kernel(const SourceArgs a) {
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int nx = a.n[0], ny = a.n[1], nz = a.n[2];
+    if (e >= (long long)nx * ny * nz) return;
+    const int i = (int)(e % nx);
+    const long long t = e / nx;
+    const int j = (int)(t % ny);
+    const int k = (int)(t / ny);
+    const int Qx = a.q[0], Qy = a.q[1];
+    const AxisDev& X = a.ax[0];
+    const int wx = X.wq, psx = X.pstart[i], cx = X.pcount[i];
+    const int wy = a.dim >= 2 ? a.ax[1].wq : 1, psy = a.dim >= 2 ? a.ax[1].pstart[j] : 0;
+    const int cy = a.dim >= 2 ? a.ax[1].pcount[j] : 1;
+    const int wz = a.dim >= 3 ? a.ax[2].wq : 1, psz = a.dim >= 3 ? a.ax[2].pstart[k] : 0;
+    const int cz = a.dim >= 3 ? a.ax[2].pcount[k] : 1;
+    using FT = typename std::conditional<IN_F32 != 0, float, double>::type;
+    CT tx[MAXW], ty[MAXW];
+#pragma unroll
+    for (int c = 0; c < MAXW; ++c) {
+        tx[c] = c < cx ? tab<CT>(X.TW, i * wx + c) : zero_v<CT>();
+        ty[c] = (a.dim < 2) ? (c == 0 ? from_double<CT>(1.0) : zero_v<CT>())
+                            : (c < cy ? tab<CT>(a.ax[1].TW, j * wy + c) : zero_v<CT>());
+    }
+    Acc<CT> acc;
+    acc.init();
+    for (int az = 0; az < cz; ++az) {
+        const int qz = psz + az;
+        const CT tz = a.dim >= 3 ? tab<CT>(a.ax[2].TW, k * wz + az) : from_double<CT>(1.0);
+        FT fv[MAXW][MAXW];
+#pragma unroll
+        for (int by = 0; by < MAXW; ++by) {
+            const long long row = ((long long)qz * Qy + (psy + by)) * Qx + psx;
+#pragma unroll
+            for (int c = 0; c < MAXW; ++c)
+                fv[by][c] = (by < cy && c < cx) ? ((const FT*)a.f)[row + c] : FT(0);
+        }
+#pragma unroll
+        for (int by = 0; by < MAXW; ++by) {
+            if (by < cy) {
+                Acc<CT> sx;
+                sx.init();
+#pragma unroll
+                for (int c = 0; c < MAXW; ++c) {
+                    if (c < cx) {
+                        if constexpr (std::is_same<CT, double>::value) sx.add_prod(tx[c], (double)fv[by][c]);
+                        else sx.add_prod_f(tx[c], (float)fv[by][c]);
+                    }
+                }
+                if constexpr (std::is_same<CT, double>::value) acc.add_prod(tz * ty[by], sx.result());
+                else acc.add_prod(df_mul(tz, ty[by]), sx.result());
+            }
+        }
+    }
+    const CT r = acc.result();
+    if constexpr (std::is_same<CT, double>::value) {
+        ((double*)a.out)[e] = r;
+    } else {
+        ((float*)a.out)[e] = r.hi;
+        ((float*)a.out)[e + a.ntot] = r.lo;
+    }
+}
+
 // PW source with the x-window of every sample row loaded before it is summed
 // (up to MAXW points per cell and axis, predicated): the loads of a row are in
 // flight together instead of one per dependent compensated product.
 template <typename CT, int IN_F32, int MAXW>
-__global__ void __launch_bounds__(256) source_pw_rows_kernel(const SourceArgs a) {
+__global__ void __launch_bounds__(256) source_pw_xrow_kernel(const SourceArgs a) {
     const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const int nx = a.n[0], ny = a.n[1], nz = a.n[2];
     if (e >= (long long)nx * ny * nz) return;
@@ -284,16 +351,17 @@ cudaError_t launch_source(const SourceArgs& a, int fp64, cudaStream_t st) {
     if (a.pw) {
         const long long total = (long long)a.n[0] * a.n[1] * a.n[2];
         const unsigned blocks = (unsigned)((total + 255) / 256);
-        const int wx = a.ax[0].wq;
-        if (wx <= 4) {
+        int wmax = a.ax[0].wq;
+        for (int k = 1; k < a.dim; ++k) wmax = std::max(wmax, a.ax[k].wq);
+        if (wmax <= 4) {
             if (fp64) source_pw_rows_kernel<double, 0, 4><<<blocks, 256, 0, st>>>(a);
             else source_pw_rows_kernel<DF, 1, 4><<<blocks, 256, 0, st>>>(a);
-        } else if (wx <= 8) {
-            if (fp64) source_pw_rows_kernel<double, 0, 8><<<blocks, 256, 0, st>>>(a);
-            else source_pw_rows_kernel<DF, 1, 8><<<blocks, 256, 0, st>>>(a);
-        } else if (wx <= 16) {
-            if (fp64) source_pw_rows_kernel<double, 0, 16><<<blocks, 256, 0, st>>>(a);
-            else source_pw_rows_kernel<DF, 1, 16><<<blocks, 256, 0, st>>>(a);
+        } else if (a.ax[0].wq <= 8) {
+            if (fp64) source_pw_xrow_kernel<double, 0, 8><<<blocks, 256, 0, st>>>(a);
+            else source_pw_xrow_kernel<DF, 1, 8><<<blocks, 256, 0, st>>>(a);
+        } else if (a.ax[0].wq <= 16) {
+            if (fp64) source_pw_xrow_kernel<double, 0, 16><<<blocks, 256, 0, st>>>(a);
+            else source_pw_xrow_kernel<DF, 1, 16><<<blocks, 256, 0, st>>>(a);
         } else {
             if (fp64) source_pw_kernel<double, 0><<<blocks, 256, 0, st>>>(a);
             else source_pw_kernel<DF, 1><<<blocks, 256, 0, st>>>(a);
