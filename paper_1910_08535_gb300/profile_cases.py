@@ -4,6 +4,7 @@
   python -m paper_1910_08535_gb300.profile_cases heat3d-step   # 3 explicit steps, 131^3, PW, FP32 pairs
   python -m paper_1910_08535_gb300.profile_cases poisson2d     # 3 solves, 2D 1024^2, cubic PW, FP32 pairs
   python -m paper_1910_08535_gb300.profile_cases batch512      # 2 batched solves, 512 uneven 2D instances
+  python -m paper_1910_08535_gb300.profile_cases source3d      # 3 PW source RHS, 128^3 quadratic, 2 points per cell
 
 Each case builds the library if needed, runs on cuda:0 and prints 'ok'.
 """
@@ -52,7 +53,24 @@ def batch512():
     bt.close()
 
 
-CASES = {'heat3d-step': heat3d_step, 'poisson2d': poisson2d, 'batch512': batch512}
+def source3d():
+    import numpy as np
+    import torch
+    from . import workloads
+    from .igapw import Context
+    c = Context(dim=3, n_elem=128, degree=2, nq=2, test='pw', precision='fp32r', op='mass')
+    pts = [c.quad_points(a)[0] for a in range(3)]
+    cub = [lambda x: 2 * x ** 3 - x ** 2 + 0.5 * x + 1, lambda x: x ** 3 + 0.3 * x + 0.2,
+           lambda x: -x ** 3 + 2 * x ** 2 + 1]
+    f = torch.from_numpy(workloads.tensor_samples(pts, [tuple(cub)]).astype(np.float32)).cuda()
+    b = c.empty()
+    for _ in range(3):
+        c.rhs_source(f, out=b)
+    c.sync()
+    c.close()
+
+
+CASES = {'heat3d-step': heat3d_step, 'poisson2d': poisson2d, 'batch512': batch512, 'source3d': source3d}
 
 
 def main(argv):
