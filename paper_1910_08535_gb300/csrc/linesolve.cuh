@@ -24,6 +24,7 @@ struct SolveSmem {
     const T* H;
     const T* PhiF;
     const T* PhiB;
+    int lanes;          // lane stride of the scan operators: 32 in global memory, P when staged
 };
 
 // Copies count elements with UNR independent loads in flight per thread
@@ -46,24 +47,30 @@ __device__ __forceinline__ void batched_copy(int count, Ld&& ld, St&& st) {
     }
 }
 
+// Scan levels of a P-chunk partition (levels 0 .. log2(P) - 1 are used).
+__host__ __device__ constexpr int scan_levels(int P) { return P <= 1 ? 0 : (P <= 2 ? 1 : (P <= 4 ? 2 : (P <= 8 ? 3 : (P <= 16 ? 4 : 5)))); }
+
+// Shared-memory elements of one axis' staged tables: LU rows and spikes, and
+// the scan operators of the P lanes and log2(P) levels actually used.
 template <typename T, int KP>
-__host__ __device__ constexpr size_t table_elems(int n) {
-    return (size_t)4 * n * KP + n + 2 * 5 * 32 * KP * KP;
+__host__ __device__ constexpr size_t table_elems(int n, int P) {
+    return (size_t)4 * n * KP + n + (size_t)2 * scan_levels(P) * P * KP * KP;
 }
 
 // Copies the LineSys tables into shared memory at `base` with asynchronous
 // copies (the caller waits: cp_async_wait_all + __syncthreads); returns the views.
 template <typename T, int KP>
 __device__ SolveSmem<T> stage_tables(const LineSys<T>& S, T* base) {
-    const int n = S.n;
+    const int n = S.n, P = S.P;
+    const int nlev = scan_levels(P);
     T* L = base;
     T* U = L + n * KP;
     T* G = U + n * KP;
     T* H = G + n * KP;
     T* dinv = H + n * KP;
     T* PhiF = dinv + n;
-    T* PhiB = PhiF + 5 * 32 * KP * KP;
-    const int nk = n * KP, nphi = 5 * 32 * KP * KP;
+    T* PhiB = PhiF + nlev * P * KP * KP;
+    const int nk = n * KP, pp = KP * KP, nphi = nlev * P * pp;
     auto cp = [](T* d, const T* s) {
         if constexpr (sizeof(T) == 8) cp_async8(d, s);
         else cp_async4(d, s);
@@ -75,11 +82,14 @@ __device__ SolveSmem<T> stage_tables(const LineSys<T>& S, T* base) {
         cp(H + e, S.H + e);
     }
     for (int e = threadIdx.x; e < n; e += blockDim.x) cp(dinv + e, S.dinv + e);
+    // scan operators: entry (level lv, lane k) moves from lane stride 32 to P
     for (int e = threadIdx.x; e < nphi; e += blockDim.x) {
-        cp(PhiF + e, S.PhiF + e);
-        cp(PhiB + e, S.PhiB + e);
+        const int blk = e / pp, r = e - blk * pp;
+        const int lv = blk / P, k = blk - lv * P;
+        cp(PhiF + e, S.PhiF + (lv * 32 + k) * pp + r);
+        cp(PhiB + e, S.PhiB + (lv * 32 + k) * pp + r);
     }
-    return SolveSmem<T>{L, U, dinv, G, H, PhiF, PhiB};
+    return SolveSmem<T>{L, U, dinv, G, H, PhiF, PhiB, P};
 }
 
 // One lane group (P lanes, chunk k = lane index in the group) solves nb <= NB
@@ -124,7 +134,7 @@ __device__ __forceinline__ void group_solve(T* x, const int st, const int lst, c
         const int d = 1 << lv;
         if (d >= P) break;   // uniform over the warp
         const bool upd = k >= d;
-        const T* Ph = S.PhiF + (lv * 32 + k) * KP * KP;
+        const T* Ph = S.PhiF + (lv * S.lanes + k) * KP * KP;
         T ph[KP * KP];
 #pragma unroll
         for (int e = 0; e < KP * KP; ++e) ph[e] = upd ? Ph[e] : T(0);
@@ -189,7 +199,7 @@ __device__ __forceinline__ void group_solve(T* x, const int st, const int lst, c
         const int d = 1 << lv;
         if (d >= P) break;
         const bool upd = k + d < P;
-        const T* Ph = S.PhiB + (lv * 32 + k) * KP * KP;
+        const T* Ph = S.PhiB + (lv * S.lanes + k) * KP * KP;
         T ph[KP * KP];
 #pragma unroll
         for (int e = 0; e < KP * KP; ++e) ph[e] = upd ? Ph[e] : T(0);
@@ -285,7 +295,7 @@ __device__ __forceinline__ void group_solve_reg(T* x, const int st, const int ls
         const int d = 1 << lv;
         if (d >= P) break;
         const bool upd = k >= d;
-        const T* Ph = S.PhiF + (lv * 32 + k) * KP * KP;
+        const T* Ph = S.PhiF + (lv * S.lanes + k) * KP * KP;
         T ph[KP * KP];
 #pragma unroll
         for (int e = 0; e < KP * KP; ++e) ph[e] = upd ? Ph[e] : T(0);
@@ -346,7 +356,7 @@ __device__ __forceinline__ void group_solve_reg(T* x, const int st, const int ls
         const int d = 1 << lv;
         if (d >= P) break;
         const bool upd = k + d < P;
-        const T* Ph = S.PhiB + (lv * 32 + k) * KP * KP;
+        const T* Ph = S.PhiB + (lv * S.lanes + k) * KP * KP;
         T ph[KP * KP];
 #pragma unroll
         for (int e = 0; e < KP * KP; ++e) ph[e] = upd ? Ph[e] : T(0);

@@ -50,7 +50,7 @@ __global__ void __launch_bounds__(256) solve_x_kernel(SolveArgs s, LineSys<T> S,
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* tabs = reinterpret_cast<T*>(smem_raw);
     const int nx = s.n[0];
-    T* buf = tabs + table_elems<T, KP>(nx);
+    T* buf = tabs + table_elems<T, KP>(nx, S.P);
     __shared__ int bnd[33];
     const int pitch = nx | 1;   // odd pitch: lanes on different lines hit different banks
     const long long nlines = (long long)s.n[1] * s.n[2];
@@ -109,7 +109,7 @@ __global__ void __launch_bounds__(256) solve_strided_kernel(SolveArgs s, LineSys
                                                             int NO, int lgNO, long long os, long long rs) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* tabs = reinterpret_cast<T*>(smem_raw);
-    T* buf = tabs + table_elems<T, KP>(nline);
+    T* buf = tabs + table_elems<T, KP>(nline, S.P);
     __shared__ int bnd[33];
     const int nx = s.n[0];
     const int x0 = blockIdx.x * 32;
@@ -174,7 +174,7 @@ __global__ void __launch_bounds__(256) solve_cols_kernel(SolveArgs s, LineSys<T>
     const int x0 = blockIdx.x * CW;
     const int nc = min(CW, nx - x0);
     const int pitch = CW + 1;
-    const SolveSmem<T> st{S.L, S.U, S.dinv, S.G, S.H, S.PhiF, S.PhiB};
+    const SolveSmem<T> st{S.L, S.U, S.dinv, S.G, S.H, S.PhiF, S.PhiB, 32};
     for (int e = threadIdx.x; e < 33; e += blockDim.x) bnd[e] = S.b[e];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int c = lane & (CW - 1), r0 = lane >> lgCW, rpw = 32 >> lgCW;
@@ -218,7 +218,7 @@ static cudaError_t run_solve(const SolveArgs& s, const LineSys<T>& S, cudaStream
     if (s.axis == 0) {
         const int nx = s.n[0];
         const long long nlines = (long long)s.n[1] * s.n[2];
-        const size_t tb = table_elems<T, KP>(nx) * sizeof(T);
+        const size_t tb = table_elems<T, KP>(nx, S.P) * sizeof(T);
         int warps = 8;
         while (warps > 1 && tb + (size_t)warps * lines_per_warp * (nx | 1) * sizeof(T) > 100 * 1024) warps >>= 1;
         const int lpb = warps * lines_per_warp;
@@ -237,7 +237,7 @@ static cudaError_t run_solve(const SolveArgs& s, const LineSys<T>& S, cudaStream
         // NO outer indices x 32 columns per block; one warp per lines_per_warp lines
         int NO = 1;
         while (NO * 32 < 8 * lines_per_warp && NO < outer) NO *= 2;
-        const size_t tb = table_elems<T, KP>(nline) * sizeof(T);
+        const size_t tb = table_elems<T, KP>(nline, S.P) * sizeof(T);
         while (NO > 1 && tb + (size_t)nline * (NO * 32 + 1) * sizeof(T) > 100 * 1024) NO >>= 1;
         const int warps = std::min(8, (NO * 32 + lines_per_warp - 1) / lines_per_warp);
         const size_t sm = tb + (size_t)nline * (NO * 32 + 1) * sizeof(T);

@@ -97,7 +97,7 @@ __global__ void __launch_bounds__(256) axis_step_kernel(const AxisStepArgs a) {
     const VT* At;
     const int* fs;
     if constexpr (TG) {
-        S = SolveSmem<TS>{LS.L, LS.U, LS.dinv, LS.G, LS.H, LS.PhiF, LS.PhiB};
+        S = SolveSmem<TS>{LS.L, LS.U, LS.dinv, LS.G, LS.H, LS.PhiF, LS.PhiB, 32};
         if constexpr (DFM) {
             Ct = reinterpret_cast<const VT*>(AX.C.df);
             At = reinterpret_cast<const VT*>(AX.A.df);
@@ -108,7 +108,7 @@ __global__ void __launch_bounds__(256) axis_step_kernel(const AxisStepArgs a) {
         fs = AX.fstart;
     } else {
         TS* tabs = reinterpret_cast<TS*>(p);
-        p += align16(table_elems<TS, KP>(n) * sizeof(TS));
+        p += align16(table_elems<TS, KP>(n, LS.P) * sizeof(TS));
         VT* ct = reinterpret_cast<VT*>(p);
         VT* at = ct + n * W;
         p += align16((size_t)2 * n * W * sizeof(VT));
@@ -360,7 +360,7 @@ static cudaError_t run_axis_step(const AxisStepArgs& a0, cudaStream_t st) {
         const size_t cap = xl ? (size_t)nl * ((n + W) | 1) : (size_t)(n + W) * (nl + 1);
         size_t b = (size_t)2 * cap * sizeof(VT);
         if (!tg)
-            b += align16(table_elems<TS, KP>(n) * sizeof(TS)) + align16((size_t)2 * n * W * sizeof(VT)) +
+            b += align16(table_elems<TS, KP>(n, a.ax.ls64.P) * sizeof(TS)) + align16((size_t)2 * n * W * sizeof(VT)) +
                  align16((size_t)n * sizeof(int));
         return b;
     };
