@@ -251,7 +251,11 @@ int igapw_solve(igapw_ctx* ctx, const void* r_dev, void* u_dev);
  * scheme with a different rounding order.  With IGAPW_FLAG_STEP_RHS_SOLVE the
  * step forms the RHS with igapw_apply(HEAT) and solves with igapw_solve.
  * Needs a mass-matrix context (op != POISSON).  The step sequence is captured
- * once per (dt, nsteps, u_dev) into a CUDA graph and replayed. Asynchronous. */
+ * once per (dt, nsteps, u_dev) into a CUDA graph and replayed. Asynchronous,
+ * except the first split-form call on a context: it times the launch shapes of
+ * the per-axis kernel (staged or global tables, lines or columns per block) on
+ * scratch tensors and waits for the context stream, so that call must not be
+ * made inside a stream capture. */
 int igapw_step(igapw_ctx* ctx, double dt, int nsteps, void* u_dev);
 
 /* Same as igapw_step with HOST buffers: copies u_host (pinned memory gives an
