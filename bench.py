@@ -211,18 +211,11 @@ def _time_events(stream, fn, reps, flush=None, warm=3):
     return sum(out) / len(out)
 
 
-def measure_rows(ctx_pw, u, dt, stream, flush, hbm_peak):
-    """Rows a3 (operator action) and a6 (refined Kronecker solve) on heat3d:
-    device time per call, bytes per DOF moved by the algorithm, and the
-    oracle's CPU time for the same operation."""
-    import numpy as np
+def cpu_baseline_rows(dt):
+    """CPU-baseline leg of rows a3 / a6: the oracle's operator action and
+    Kronecker solve on the same heat3d state, timed on the host cores."""
     from oracle import systems, tensor
     from paper_1910_08535_gb300 import workloads
-    n = ctx_pw.ntot
-    r = ctx_pw.empty()
-    out = ctx_pw.empty()
-    t_apply = _time_events(stream, lambda: ctx_pw.apply('heat', u, dt, out=r), 10, flush)
-    t_solve = _time_events(stream, lambda: ctx_pw.solve(r, out=out), 10, flush)
     w = workloads.WORKLOADS[WORKLOAD]
     axes = [systems.Axis(w['n_elem'], w['degree'], w['nq'], 'pw') for _ in range(3)]
     M, L = tensor.mass_mats(axes), tensor.lap_mats(axes)
@@ -232,15 +225,40 @@ def measure_rows(ctx_pw, u, dt, stream, flush, hbm_peak):
     t1 = time.perf_counter()
     tensor.ads_solve(M, rr)
     t2 = time.perf_counter()
+    return t1 - t0, t2 - t1
+
+
+def measure_rows(ctx_pw, u, dt, stream, flush, hbm_peak):
+    """Rows a3 (operator action) and a6 (refined Kronecker solve) on heat3d:
+    device time per call, bytes per DOF moved by the algorithm, and the
+    oracle's CPU time for the same operation."""
+    n = ctx_pw.ntot
+    r = ctx_pw.empty()
+    out = ctx_pw.empty()
+    t_apply = _time_events(stream, lambda: ctx_pw.apply('heat', u, dt, out=r), 10, flush)
+    t_solve = _time_events(stream, lambda: ctx_pw.solve(r, out=out), 10, flush)
+    cpu_apply, cpu_solve = cpu_baseline_rows(dt)
     return {
         'a3_apply_heat': {'us': t_apply * 1e6, 'dof_per_s': n / t_apply,
                           'hbm_frac_16B_per_dof': 16.0 * n / t_apply / 1e9 / hbm_peak,
                           'kernel': 'contract_kernel (7 double-float banded passes)',
-                          'oracle_cpu_s': t1 - t0},
+                          'oracle_cpu_s': cpu_apply},
         'a6_solve_refined': {'us': t_solve * 1e6, 'dof_per_s': n / t_solve,
                              'kernels': '3 FP32 line solves + double-float residual + 3 line solves',
-                             'oracle_cpu_s': t2 - t1},
+                             'oracle_cpu_s': cpu_solve},
     }
+
+
+def cpu_baseline_source(ne, p, nq, test, f, got):
+    """CPU-baseline leg of row a4: the oracle's source RHS from the same
+    samples, timed on the host cores, and the GPU result's rel-L2 against it."""
+    import numpy as np
+    from oracle import systems, tensor
+    axes = [systems.Axis(ne, p, nq, test) for _ in range(3)]
+    t0 = time.perf_counter()
+    ref = tensor.rhs_source(axes, f.astype(np.float64))
+    tcpu = time.perf_counter() - t0
+    return float(np.linalg.norm(got - ref) / np.linalg.norm(ref)), tcpu
 
 
 def measure_source_table1(stream, flush, hbm_peak, reps=5):
@@ -251,7 +269,6 @@ def measure_source_table1(stream, flush, hbm_peak, reps=5):
     rule's points (FP32), the RHS accumulates in double-float."""
     import numpy as np
     import torch
-    from oracle import systems, tensor
     from paper_1910_08535_gb300 import workloads
     from paper_1910_08535_gb300.igapw import Context
     ne, p = 128, 2
@@ -269,13 +286,7 @@ def measure_source_table1(stream, flush, hbm_peak, reps=5):
         q = [len(x) for x in pts]
         fbytes = 4 * q[0] * q[1] * q[2]
         alg = fbytes + 8 * c.ntot
-        axes = [systems.Axis(ne, p, nq, test) for _ in range(3)]
-        fh = f.cpu().numpy().astype(np.float64)
-        t0 = time.perf_counter()
-        ref = tensor.rhs_source(axes, fh)
-        tcpu = time.perf_counter() - t0
-        got = c.to_numpy(b)
-        err = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+        err, tcpu = cpu_baseline_source(ne, p, nq, test, f.cpu().numpy(), c.to_numpy(b))
         res[test] = {'nq': nq, 'points': q[0] * q[1] * q[2], 'us': t * 1e6, 'dof_per_s': c.ntot / t,
                      'alg_bytes': alg, 'achieved_gbs': alg / t / 1e9, 'hbm_frac': alg / t / 1e9 / hbm_peak,
                      'rel_l2_vs_oracle': err, 'oracle_cpu_s': tcpu}
