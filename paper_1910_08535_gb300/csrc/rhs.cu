@@ -1,6 +1,7 @@
 // Kernel (b): contraction launch dispatch (operator, system and residual
 // modes; the kernel template is in contract.cuh) and the source RHS kernels.
 #include <algorithm>
+#include <climits>
 #include <type_traits>
 
 #include "contract.cuh"
@@ -212,22 +213,25 @@ __global__ void __launch_bounds__(256) neumann_face_kernel(const NeumannArgs a) 
 // PW source, loads batched: for every z point of the cell, the whole y-by-x
 // slab of the cell's samples (its own point counts, at most MAXW per axis) is
 // loaded before it is summed, so a thread keeps up to MAXW^2 loads in flight.
+// MAXW is the largest point count per cell over the axes (2, 3 or 4): the slab
+// loops are unrolled and predicated, so a MAXW above the real counts would
+// issue the masked-off compensated products all the same.  One thread per
+// coefficient (i, j) of a z-plane (32-bit index; the host keeps nx * ny below
+// 2^31 - 256); the grid's y dimension walks the planes, and the x and y test
+// weights are loaded once per thread.
 template <typename CT, int IN_F32, int MAXW>
 __global__ void __launch_bounds__(256) source_pw_rows_kernel(const SourceArgs a) {
-    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const int nx = a.n[0], ny = a.n[1], nz = a.n[2];
-    if (e >= (long long)nx * ny * nz) return;
-    const int i = (int)(e % nx);
-    const long long t = e / nx;
-    const int j = (int)(t % ny);
-    const int k = (int)(t / ny);
+    const int plane = nx * ny;
+    const int pe = blockIdx.x * blockDim.x + threadIdx.x;
+    if (pe >= plane) return;
+    const int j = pe / nx;
+    const int i = pe - j * nx;
     const int Qx = a.q[0], Qy = a.q[1];
     const AxisDev& X = a.ax[0];
     const int wx = X.wq, psx = X.pstart[i], cx = X.pcount[i];
     const int wy = a.dim >= 2 ? a.ax[1].wq : 1, psy = a.dim >= 2 ? a.ax[1].pstart[j] : 0;
     const int cy = a.dim >= 2 ? a.ax[1].pcount[j] : 1;
-    const int wz = a.dim >= 3 ? a.ax[2].wq : 1, psz = a.dim >= 3 ? a.ax[2].pstart[k] : 0;
-    const int cz = a.dim >= 3 ? a.ax[2].pcount[k] : 1;
     using FT = typename std::conditional<IN_F32 != 0, float, double>::type;
     CT tx[MAXW], ty[MAXW];
 #pragma unroll
@@ -236,42 +240,47 @@ __global__ void __launch_bounds__(256) source_pw_rows_kernel(const SourceArgs a)
         ty[c] = (a.dim < 2) ? (c == 0 ? from_double<CT>(1.0) : zero_v<CT>())
                             : (c < cy ? tab<CT>(a.ax[1].TW, j * wy + c) : zero_v<CT>());
     }
-    Acc<CT> acc;
-    acc.init();
-    for (int az = 0; az < cz; ++az) {
-        const int qz = psz + az;
-        const CT tz = a.dim >= 3 ? tab<CT>(a.ax[2].TW, k * wz + az) : from_double<CT>(1.0);
-        FT fv[MAXW][MAXW];
+    for (int k = blockIdx.y; k < nz; k += gridDim.y) {
+        const long long e = (long long)k * plane + pe;
+        const int wz = a.dim >= 3 ? a.ax[2].wq : 1, psz = a.dim >= 3 ? a.ax[2].pstart[k] : 0;
+        const int cz = a.dim >= 3 ? a.ax[2].pcount[k] : 1;
+        Acc<CT> acc;
+        acc.init();
+        for (int az = 0; az < cz; ++az) {
+            const int qz = psz + az;
+            const CT tz = a.dim >= 3 ? tab<CT>(a.ax[2].TW, k * wz + az) : from_double<CT>(1.0);
+            FT fv[MAXW][MAXW];
 #pragma unroll
-        for (int by = 0; by < MAXW; ++by) {
-            const long long row = ((long long)qz * Qy + (psy + by)) * Qx + psx;
+            for (int by = 0; by < MAXW; ++by) {
+                const long long row = ((long long)qz * Qy + (psy + by)) * Qx + psx;
 #pragma unroll
-            for (int c = 0; c < MAXW; ++c)
-                fv[by][c] = (by < cy && c < cx) ? ((const FT*)a.f)[row + c] : FT(0);
-        }
+                for (int c = 0; c < MAXW; ++c)
+                    fv[by][c] = (by < cy && c < cx) ? ((const FT*)a.f)[row + c] : FT(0);
+            }
 #pragma unroll
-        for (int by = 0; by < MAXW; ++by) {
-            if (by < cy) {
-                Acc<CT> sx;
-                sx.init();
+            for (int by = 0; by < MAXW; ++by) {
+                if (by < cy) {
+                    Acc<CT> sx;
+                    sx.init();
 #pragma unroll
-                for (int c = 0; c < MAXW; ++c) {
-                    if (c < cx) {
-                        if constexpr (std::is_same<CT, double>::value) sx.add_prod(tx[c], (double)fv[by][c]);
-                        else sx.add_prod_f(tx[c], (float)fv[by][c]);
+                    for (int c = 0; c < MAXW; ++c) {
+                        if (c < cx) {
+                            if constexpr (std::is_same<CT, double>::value) sx.add_prod(tx[c], (double)fv[by][c]);
+                            else sx.add_prod_f(tx[c], (float)fv[by][c]);
+                        }
                     }
+                    if constexpr (std::is_same<CT, double>::value) acc.add_prod(tz * ty[by], sx.result());
+                    else acc.add_prod(df_mul(tz, ty[by]), sx.result());
                 }
-                if constexpr (std::is_same<CT, double>::value) acc.add_prod(tz * ty[by], sx.result());
-                else acc.add_prod(df_mul(tz, ty[by]), sx.result());
             }
         }
-    }
-    const CT r = acc.result();
-    if constexpr (std::is_same<CT, double>::value) {
-        ((double*)a.out)[e] = r;
-    } else {
-        ((float*)a.out)[e] = r.hi;
-        ((float*)a.out)[e + a.ntot] = r.lo;
+        const CT r = acc.result();
+        if constexpr (std::is_same<CT, double>::value) {
+            ((double*)a.out)[e] = r;
+        } else {
+            ((float*)a.out)[e] = r.hi;
+            ((float*)a.out)[e + a.ntot] = r.lo;
+        }
     }
 }
 
@@ -353,9 +362,19 @@ cudaError_t launch_source(const SourceArgs& a, int fp64, cudaStream_t st) {
         const unsigned blocks = (unsigned)((total + 255) / 256);
         int wmax = a.ax[0].wq;
         for (int k = 1; k < a.dim; ++k) wmax = std::max(wmax, a.ax[k].wq);
-        if (wmax <= 4) {
-            if (fp64) source_pw_rows_kernel<double, 0, 4><<<blocks, 256, 0, st>>>(a);
-            else source_pw_rows_kernel<DF, 1, 4><<<blocks, 256, 0, st>>>(a);
+        const long long plane = (long long)a.n[0] * a.n[1];
+        if (wmax <= 4 && plane <= INT_MAX - 256) {
+            const dim3 grid((unsigned)((plane + 255) / 256), (unsigned)std::min(a.n[2], 65535));
+            if (wmax <= 2) {
+                if (fp64) source_pw_rows_kernel<double, 0, 2><<<grid, 256, 0, st>>>(a);
+                else source_pw_rows_kernel<DF, 1, 2><<<grid, 256, 0, st>>>(a);
+            } else if (wmax == 3) {
+                if (fp64) source_pw_rows_kernel<double, 0, 3><<<grid, 256, 0, st>>>(a);
+                else source_pw_rows_kernel<DF, 1, 3><<<grid, 256, 0, st>>>(a);
+            } else {
+                if (fp64) source_pw_rows_kernel<double, 0, 4><<<grid, 256, 0, st>>>(a);
+                else source_pw_rows_kernel<DF, 1, 4><<<grid, 256, 0, st>>>(a);
+            }
         } else if (a.ax[0].wq <= 8) {
             if (fp64) source_pw_xrow_kernel<double, 0, 8><<<blocks, 256, 0, st>>>(a);
             else source_pw_xrow_kernel<DF, 1, 8><<<blocks, 256, 0, st>>>(a);

@@ -78,15 +78,17 @@ def test_apply_solve_step(d, ne, p, test, prec):
     c2.close()
 
 
-@pytest.mark.parametrize('d,ne', [(1, 9), (2, [6, 5]), (3, [4, 3, 5])])
+# (p, nq): at most 2, 3 or 4 sample points per PW cell and axis (the slab
+# kernel's unroll widths), and 8 (p = 3 cells straddle a knot: two pieces)
+@pytest.mark.parametrize('p,nq', [(2, 2), (2, 3), (3, 2), (3, 4)])
+@pytest.mark.parametrize('d,ne', [(1, 9), (2, [6, 5]), (3, [4, 3, 5]), (2, [300, 7]), (3, [37, 21, 5])])
 @pytest.mark.parametrize('test', ['pw', 'galerkin'])
 @pytest.mark.parametrize('prec', ['fp64', 'fp32r'])
-def test_source_rhs(d, ne, test, prec):
+def test_source_rhs(d, ne, test, prec, p, nq):
     import torch
     from paper_1910_08535_gb300 import workloads
-    p = 2
-    c = _ctx(dim=d, n_elem=ne, degree=p, nq=3, test=test, precision=prec)
-    axes = oracle_axes(d, ne, p, 3, test)
+    c = _ctx(dim=d, n_elem=ne, degree=p, nq=nq, test=test, precision=prec)
+    axes = oracle_axes(d, ne, p, nq, test)
     pts = [c.quad_points(a)[0] for a in range(d)]
     f = workloads.tensor_samples(pts, [tuple(np.sin for _ in range(d)), tuple((lambda x: x ** 2) for _ in range(d))])
     fd = torch.from_numpy(f.astype(np.float64 if prec == 'fp64' else np.float32)).cuda()
