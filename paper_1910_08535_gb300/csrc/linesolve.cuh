@@ -402,8 +402,8 @@ __device__ __forceinline__ void group_solve_reg(T* x, const int st, const int ls
     }
 }
 
-// Sequential solve of one whole line by one lane (P = 1), for batches with
-// many lines.  Values stream through a register prefetch ring of D rows so no
+// Sequential solve of one whole line by one lane (P = 1), for short lines
+// (at most 20 rows, or too few rows for two chunks of p).  Values stream through a register prefetch ring of D rows so no
 // shared-memory load sits on the recurrence; the farthest band entries are
 // applied first so each row waits on its predecessor for one FMA.
 template <typename T, int KP, int D>
