@@ -101,6 +101,27 @@ def _check(rc, ctx=None):
         raise IgapwError(rc, msg.decode() if msg else '')
 
 
+def _check_tensor(t, what, dtype, numel):
+    """Argument check of the Context helpers: a torch tensor that the library
+    would address on the host, reinterpret or run past the end of (not on a
+    CUDA device, another dtype, not contiguous, another element count) raises
+    IgapwError(IGAPW_ERR_ARG) before the call.  Raw pointers (ints) are the
+    caller's responsibility and pass unchecked."""
+    if not hasattr(t, 'is_cuda'):
+        return
+    if not t.is_cuda:
+        problem = 'not on a CUDA device'
+    elif t.dtype != dtype:
+        problem = f'dtype {t.dtype}, expected {dtype}'
+    elif not t.is_contiguous():
+        problem = 'not contiguous'
+    elif t.numel() != numel:
+        problem = f'{t.numel()} elements, expected {numel}'
+    else:
+        return
+    raise IgapwError(IGAPW_ERR_ARG, f'{what}: {problem}')
+
+
 def _dptr(a):
     return ctypes.cast(ctypes.c_void_p(a.data_ptr() if hasattr(a, 'data_ptr') else int(a)), ctypes.c_void_p)
 
@@ -276,6 +297,31 @@ class Context:
         self.ntot, dims = igapw_size(self.ctx)
         self.n = dims                                   # (n_x, n_y, n_z)
         self.shape = tuple(reversed(dims[:dim]))        # (n_z, n_y, n_x)[-dim:]
+        self._count_points()
+
+    def _count_points(self):
+        """Quadrature points per axis (the sample grid of rhs_source)."""
+        self.q = []
+        for a in range(self.dim):
+            cnt = _I()
+            _check(load().igapw_quad_points(self.ctx, a, None, None, ctypes.byref(cnt)), self.ctx)
+            self.q.append(cnt.value)
+
+    def _coefs(self, t, what):
+        import torch
+        if self.precision == 'fp64':
+            _check_tensor(t, what, torch.float64, self.ntot)
+        else:
+            _check_tensor(t, what, torch.float32, 2 * self.ntot)
+        return t
+
+    def _samples(self, t, what, axes):
+        import torch
+        numel = 1
+        for a in axes:
+            numel *= self.q[a]
+        _check_tensor(t, what, torch.float64 if self.precision == 'fp64' else torch.float32, numel)
+        return t
 
     # tensors --------------------------------------------------------------
     def empty(self):
@@ -304,27 +350,29 @@ class Context:
 
     # calls -------------------------------------------------------------------
     def apply(self, op, u, dt=0.0, out=None):
-        out = self.empty() if out is None else out
-        igapw_apply(self.ctx, OPS[op], dt, u, out)
+        out = self.empty() if out is None else self._coefs(out, 'apply: out')
+        igapw_apply(self.ctx, OPS[op], dt, self._coefs(u, 'apply: u'), out)
         return out
 
     def solve(self, r, out=None):
-        out = self.empty() if out is None else out
-        igapw_solve(self.ctx, r, out)
+        out = self.empty() if out is None else self._coefs(out, 'solve: out')
+        igapw_solve(self.ctx, self._coefs(r, 'solve: r'), out)
         return out
 
     def step(self, u, dt, nsteps):
-        igapw_step(self.ctx, dt, nsteps, u)
+        igapw_step(self.ctx, dt, nsteps, self._coefs(u, 'step: u'))
         return u
 
     def rhs_source(self, f, out=None):
-        out = self.empty() if out is None else out
-        igapw_rhs_source(self.ctx, f, out)
+        out = self.empty() if out is None else self._coefs(out, 'rhs_source: out')
+        igapw_rhs_source(self.ctx, self._samples(f, 'rhs_source: f', range(self.dim)), out)
         return out
 
     def rhs_neumann(self, axis, side, g, b):
         """b += the Neumann data term of the end face `side` of `axis` (in place)."""
-        igapw_rhs_neumann(self.ctx, axis, side, g, b)
+        if 0 <= axis < self.dim:
+            self._samples(g, 'rhs_neumann: g', [a for a in range(self.dim) if a != axis])
+        igapw_rhs_neumann(self.ctx, axis, side, g, self._coefs(b, 'rhs_neumann: b'))
         return b
 
     def quad_points(self, axis):
@@ -338,6 +386,7 @@ class Context:
 
     def set_knots(self, axis, knots):
         igapw_set_knots(self.ctx, axis, knots)
+        self._count_points()
 
     def sync(self):
         igapw_sync_status(self.ctx)

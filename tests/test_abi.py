@@ -52,3 +52,35 @@ def test_missing_library_fails_loudly(tmp_path):
             igapw.load(str(tmp_path / 'nope.so'))
     finally:
         igapw._lib = saved
+
+
+class _FakeDeviceTensor:
+    """Stands in for a CUDA tensor on a machine without a GPU."""
+
+    def __init__(self, dtype, numel, contiguous=True):
+        self.is_cuda, self.dtype, self._n, self._c = True, dtype, numel, contiguous
+
+    def numel(self):
+        return self._n
+
+    def is_contiguous(self):
+        return self._c
+
+
+def test_helper_argument_checks():
+    """The Context helpers reject, with IGAPW_ERR_ARG and before any library
+    call, tensors the kernels would address on the host, reinterpret or run
+    past the end of; raw pointers pass unchecked."""
+    import torch
+    from paper_1910_08535_gb300 import igapw
+    chk = igapw._check_tensor
+    chk(_FakeDeviceTensor(torch.float32, 24), 'u', torch.float32, 24)
+    chk(12345, 'u', torch.float32, 24)
+    cases = [(torch.zeros(24, dtype=torch.float32), 'not on a CUDA device'),
+             (_FakeDeviceTensor(torch.float64, 24), 'dtype'),
+             (_FakeDeviceTensor(torch.float32, 24, contiguous=False), 'not contiguous'),
+             (_FakeDeviceTensor(torch.float32, 23), '23 elements, expected 24')]
+    for t, msg in cases:
+        with pytest.raises(igapw.IgapwError, match=msg) as ei:
+            chk(t, 'u', torch.float32, 24)
+        assert ei.value.code == igapw.IGAPW_ERR_ARG
