@@ -435,7 +435,13 @@ class Batch:
         self.handle = igapw_batch_create(descs, self.stream)
 
     def source_sine(self, params):
-        igapw_batch_source_sine(self.handle, params)
+        """params: one row (amp, kx, ky) per instance; the library reads
+        exactly instances x 3 doubles, so any other shape is rejected."""
+        import numpy as np
+        p = np.asarray(params, dtype=np.float64)
+        if p.shape != (len(self.shapes), 3):
+            raise IgapwError(IGAPW_ERR_ARG, f'source_sine: params of shape {p.shape}, expected ({len(self.shapes)}, 3)')
+        igapw_batch_source_sine(self.handle, p)
 
     def solve(self):
         igapw_batch_solve(self.handle)

@@ -84,3 +84,19 @@ def test_helper_argument_checks():
         with pytest.raises(igapw.IgapwError, match=msg) as ei:
             chk(t, 'u', torch.float32, 24)
         assert ei.value.code == igapw.IGAPW_ERR_ARG
+
+
+def test_batch_params_shape_checked(monkeypatch):
+    """Batch.source_sine passes exactly instances x 3 doubles to the library
+    (which reads that many from the host pointer); other shapes are rejected."""
+    import numpy as np
+    from paper_1910_08535_gb300 import igapw
+    seen = []
+    monkeypatch.setattr(igapw, 'igapw_batch_source_sine', lambda h, p: seen.append(p.shape))
+    b = object.__new__(igapw.Batch)
+    b.shapes, b.handle = [(8, 8, 2)] * 4, None
+    b.source_sine(np.ones((4, 3)))
+    for bad in (np.ones((3, 3)), np.ones(12), np.ones((4, 2))):
+        with pytest.raises(igapw.IgapwError, match='source_sine'):
+            b.source_sine(bad)
+    assert seen == [(4, 3)]
