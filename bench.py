@@ -146,6 +146,15 @@ def peaks():
         return {}
 
 
+def peak_sources(pk):
+    """Where each roofline denominator comes from: the machine's measured copy
+    rate and maximum SM clock (MEASURED_PEAKS.json), else the fallbacks."""
+    return {'hbm_gbs': pk.get('hbm_gbs', 6800.0),
+            'hbm_source': 'measured' if 'hbm_gbs' in pk else 'fallback (6.8 TB/s)',
+            'sm_max_mhz': pk.get('sm_max_mhz', 2070.0),
+            'clock_source': 'measured' if 'sm_max_mhz' in pk else 'nominal (2070 MHz)'}
+
+
 def cpu_baseline_oracle(test='pw', steps=20):
     """The FP64 oracle on the same workload: `steps` explicit steps at full size."""
     import numpy as np
@@ -547,7 +556,8 @@ def run_native(args, rank, world):
     W, p = 5, 3                             # PW cubic window (Galerkin: 7)
     ops_per_dof_axis = 12 * W + 3 + 11 * W + 3 + 2 * (2 * p + 1) + 21
     alg_ops = ntot * 3 * ops_per_dof_axis   # one step = 3 axis launches
-    sm_mhz = pk.get('sm_max_mhz', 2070.0)
+    src = peak_sources(pk)
+    sm_mhz = src['sm_max_mhz']
     alu_peak = 152 * 128 * sm_mhz * 1e6 / 1e12
     achieved = alg_ops / t_one / 1e12
     # DRAM bytes of one step (3 launches, x staged 32 lines, y/z staged 16 columns) from
@@ -558,9 +568,11 @@ def run_native(args, rank, world):
             'traffic': step_traffic, 'traffic_note': 'bytes per step (3 launches), ncu cold-cache replay',
             'kernel': 'axis_step_kernel<DF,3,5,*> x3 (one explicit step, PW)',
             'peak_kind': f'derived: 152 SMs x 128 FP32 lanes x {sm_mhz:.0f} MHz (FP32 operations/s, FMA = 1)',
+            'clock_source': src['clock_source'],
             'alg_ops_per_step': alg_ops, 'step_us': t_one * 1e6}
-    hbm_peak = pk.get('hbm_gbs', 6800.0)
+    hbm_peak = src['hbm_gbs']
     hbm_view = {'alg_bytes_per_dof_step': 16, 'achieved_gbs': 16.0 * ntot / t_one / 1e9, 'peak_gbs': hbm_peak,
+                'peak_source': src['hbm_source'],
                 'frac': 16.0 * ntot / t_one / 1e9 / hbm_peak,
                 'note': 'state is L2-resident across the 50 steps of a run; the step is ALU-bound (double-float)'}
 
@@ -586,6 +598,7 @@ def run_native(args, rank, world):
     rows['a7_poisson_2d_1024'] = cpu_baseline_poisson(poisson)
     rows['a8_batch_poisson_512'] = cpu_baseline_batch(measure_batch(stream))
     rows['a9_size_ladder'] = measure_ladder(stream, flush, hbm_peak)
+    rows['hbm_peak_of_the_fracs'] = {'gbs': hbm_peak, 'source': src['hbm_source']}
     # the request server is a one-GPU process: measured at N = 1
     serving = measure_serving() if (world == 1 and not args.no_serve) else None
 
