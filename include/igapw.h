@@ -146,7 +146,14 @@ int igapw_create(igapw_ctx** out, const igapw_desc* desc, void* cuda_stream);
 /* Replaces the knot vector of one axis by a caller-given open knot vector
  * (len = n_elem[axis] + 2p + 1 non-decreasing values, first and last repeated
  * p+1 times, no interior knot repeated more than p-1 times so C^1 holds) and
- * rebuilds that axis' tables and factors.  Host pointer, copied. Synchronous. */
+ * rebuilds that axis' tables and factors.  Host pointer, copied. Synchronous.
+ * Layout limit: every row of the 1D tables is stored as a window of W
+ * consecutive columns whose start advances by 0 or 1 from row to row.  With
+ * PW or refined tests, a knot vector whose element sizes change abruptly (a
+ * cell spanning several small elements next to large ones: most random knot
+ * vectors, or geometric grading above a ratio of about 1.5 per element) breaks
+ * that rule and is rejected with IGAPW_ERR_ARG and a message; B-spline tests
+ * accept any open knot vector. */
 int igapw_set_knots(igapw_ctx* ctx, int axis, const double* knots, int len);
 
 /* The 1D quadrature point set of one axis in increasing x: every element

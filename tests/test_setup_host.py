@@ -74,7 +74,22 @@ def _cases():
 
 @pytest.mark.parametrize('test,p,nq,bc,ne,uniform', list(_cases()))
 def test_host_setup_matches_oracle(dump, test, p, nq, bc, ne, uniform):
-    full = _knots(ne, p, uniform)
+    _compare(dump, test, p, nq, bc, ne, _knots(ne, p, uniform))
+
+
+@pytest.mark.parametrize('ratio', [1.05, 1.2, 1.5])
+@pytest.mark.parametrize('test', ['pw', 'galerkin', 'refined'])
+@pytest.mark.parametrize('p', [2, 3, 4])
+def test_graded_meshes(dump, ratio, test, p):
+    """Geometrically graded elements (each `ratio` times the previous, 50
+    elements): built, and equal to the oracle."""
+    h = ratio ** np.arange(50)
+    inner = np.concatenate([[0.0], np.cumsum(h) / h.sum()])
+    inner[-1] = 1.0
+    _compare(dump, test, p, p + 1, 'none', 50, np.concatenate([np.zeros(p), inner, np.ones(p)]))
+
+
+def _compare(dump, test, p, nq, bc, ne, full):
     refine = 3 if test == 'refined' else 0
     got = dump(ne, p, nq, test, bc, refine, full)
     assert 'error' not in got, got.get('error')
