@@ -179,6 +179,29 @@ def cpu_baseline_oracle(test='pw', steps=20):
             'seconds': el}
 
 
+def cpu_baseline_heat_parity(got, steps, seed=0):
+    """Precision of the headline output, with the oracle's run timed on the
+    host cores: the FP64 oracle takes the same heat3d workload (initial state,
+    dt, `steps` steps, PW tests) and the GPU result `got` (float64 array of
+    the final coefficients) is compared with it: rel-L2, max-abs and max-abs
+    relative to the largest coefficient."""
+    import numpy as np
+    from oracle import systems, tensor
+    from paper_1910_08535_gb300 import workloads
+    w = workloads.WORKLOADS[WORKLOAD]
+    axes = [systems.Axis(w['n_elem'], w['degree'], w['nq'], 'pw') for _ in range(3)]
+    M, L = tensor.mass_mats(axes), tensor.lap_mats(axes)
+    u = workloads.initial_state(WORKLOAD, seed=seed)
+    dt = workloads.dt_of(WORKLOAD)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        u = tensor.ads_solve(M, tensor.apply_heat_system(axes, u, dt, M, L))
+    el = time.perf_counter() - t0
+    d = got - u
+    return {'rel_l2': float(np.linalg.norm(d) / np.linalg.norm(u)), 'max_abs': float(np.max(np.abs(d))),
+            'max_abs_rel': float(np.max(np.abs(d)) / np.max(np.abs(u))), 'oracle_cpu_s': el}
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
@@ -589,6 +612,8 @@ def run_native(args, rank, world):
         if i >= args.warmup:
             e2e_t.append(el)
     e2e_total = max_over_ranks(sum(e2e_t), world)
+    # the pinned buffer now holds the state after the last end-to-end run
+    final_state = hb[0].astype(np.float64) + hb[1].astype(np.float64)
     e2e = {'value': world * ntot * nsteps * args.steps / e2e_total, 'unit': 'DOF-updates/s',
            'h2d_bytes_per_step': 8 * ntot, 'd2h_bytes_per_step': 8 * ntot}
 
@@ -599,6 +624,14 @@ def run_native(args, rank, world):
     rows['a8_batch_poisson_512'] = cpu_baseline_batch(measure_batch(stream))
     rows['a9_size_ladder'] = measure_ladder(stream, flush, hbm_peak)
     rows['hbm_peak_of_the_fracs'] = {'gbs': hbm_peak, 'source': src['hbm_source']}
+    if rank == 0:
+        # a failed comparison is reported in the line rather than ending the run
+        try:
+            prec = cpu_baseline_heat_parity(final_state, nsteps, seed=rank)
+        except Exception as ex:
+            prec = {'error': repr(ex)}
+        prec['output'] = f'heat3d PW state after {nsteps} steps (FP32 pairs, through igapw_step_host) vs the FP64 oracle'
+        rows['a8_precision_heat3d'] = prec
     # the request server is a one-GPU process: measured at N = 1
     serving = measure_serving() if (world == 1 and not args.no_serve) else None
 
