@@ -3,7 +3,7 @@
 The compute path is the C-ABI library ``lib/libigapw.so`` (hand-written CUDA
 kernels, see ``include/igapw.h``).  ``igapw`` is a thin ctypes binding with the
 same call names plus two convenience wrappers that allocate torch tensors of
-the right shape: ``Context`` (one problem: tables, operator action, source
+the right shape and check the ones they are given: ``Context`` (one problem: tables, operator action, source
 RHS, Kronecker solve, explicit steps, 2D/3D Poisson with Dirichlet or mixed
 boundary conditions) and ``Batch`` (many uneven 2D Poisson instances solved
 stage by stage in shared launches).  ``serve`` is a continuous-batching request
