@@ -363,6 +363,31 @@ class Context:
         igapw_step(self.ctx, dt, nsteps, self._coefs(u, 'step: u'))
         return u
 
+    def step_host(self, u_host, dt, nsteps):
+        """igapw_step_host: `nsteps` steps of a HOST state (numpy array or CPU
+        tensor, C-contiguous, float64 / float32 pair planes as on the device;
+        pinned memory makes the copies asynchronous), copied in and back,
+        synchronised before returning."""
+        import numpy as np
+        fp64 = self.precision == 'fp64'
+        numel = self.ntot if fp64 else 2 * self.ntot
+        if isinstance(u_host, np.ndarray):
+            ok = (u_host.dtype == (np.float64 if fp64 else np.float32) and u_host.flags.c_contiguous
+                  and u_host.flags.writeable and u_host.size == numel)
+            ptr = u_host.ctypes.data
+        elif hasattr(u_host, 'is_cuda') and not u_host.is_cuda:
+            import torch
+            ok = (u_host.dtype == (torch.float64 if fp64 else torch.float32) and u_host.is_contiguous()
+                  and u_host.numel() == numel)
+            ptr = u_host.data_ptr()
+        else:
+            raise IgapwError(IGAPW_ERR_ARG, 'step_host: u_host must be a numpy array or a CPU tensor')
+        if not ok:
+            raise IgapwError(IGAPW_ERR_ARG, f'step_host: expected a writable C-contiguous '
+                             f'{"float64" if fp64 else "float32"} buffer of {numel} elements')
+        igapw_step_host(self.ctx, dt, nsteps, ptr)
+        return u_host
+
     def rhs_source(self, f, out=None):
         out = self.empty() if out is None else self._coefs(out, 'rhs_source: out')
         igapw_rhs_source(self.ctx, self._samples(f, 'rhs_source: f', range(self.dim)), out)
@@ -395,6 +420,12 @@ class Context:
         if self.ctx:
             igapw_destroy(self.ctx)
             self.ctx = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
 
     def __del__(self):
         try:
@@ -466,6 +497,12 @@ class Batch:
         if self.handle:
             igapw_batch_destroy(self.handle)
             self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
 
     def __del__(self):
         try:

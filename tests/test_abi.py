@@ -100,3 +100,56 @@ def test_batch_params_shape_checked(monkeypatch):
         with pytest.raises(igapw.IgapwError, match='source_sine'):
             b.source_sine(bad)
     assert seen == [(4, 3)]
+
+
+def _bare_context(precision, ntot=24):
+    from paper_1910_08535_gb300 import igapw
+    c = object.__new__(igapw.Context)
+    c.precision, c.ntot, c.ctx = precision, ntot, None
+    return c
+
+
+def test_step_host_checks_host_buffers(monkeypatch):
+    """Context.step_host hands the library a host pointer only for a writable,
+    C-contiguous host buffer of the context's dtype and size."""
+    import numpy as np
+    import torch
+    from paper_1910_08535_gb300 import igapw
+    seen = []
+    monkeypatch.setattr(igapw, 'igapw_step_host', lambda ctx, dt, n, ptr: seen.append(ptr))
+    c = _bare_context('fp32r')
+    a = np.zeros((2, 24), dtype=np.float32)
+    c.step_host(a, 1e-3, 2)
+    t = torch.zeros(48, dtype=torch.float32)
+    c.step_host(t, 1e-3, 2)
+    assert seen == [a.ctypes.data, t.data_ptr()]
+    bad = [np.zeros(48), np.zeros(47, dtype=np.float32), np.zeros((24, 4), dtype=np.float32)[:, ::2],
+           _FakeDeviceTensor(torch.float32, 48), 12345]
+    ro = np.zeros(48, dtype=np.float32)
+    ro.flags.writeable = False
+    bad.append(ro)
+    for b in bad:
+        with pytest.raises(igapw.IgapwError, match='step_host'):
+            c.step_host(b, 1e-3, 2)
+    assert len(seen) == 2
+    c64 = _bare_context('fp64')
+    c64.step_host(np.zeros(24), 1e-3, 1)
+    with pytest.raises(igapw.IgapwError):
+        c64.step_host(np.zeros(24, dtype=np.float32), 1e-3, 1)
+
+
+def test_context_and_batch_close_on_exit(monkeypatch):
+    from paper_1910_08535_gb300 import igapw
+    closed = []
+    monkeypatch.setattr(igapw, 'igapw_destroy', lambda ctx: closed.append('ctx'))
+    monkeypatch.setattr(igapw, 'igapw_batch_destroy', lambda h: closed.append('batch'))
+    c = _bare_context('fp64')
+    c.ctx = object()
+    with c as same:
+        assert same is c
+    assert c.ctx is None
+    b = object.__new__(igapw.Batch)
+    b.handle = object()
+    with b:
+        pass
+    assert b.handle is None and closed == ['ctx', 'batch']
