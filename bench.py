@@ -426,7 +426,7 @@ def measure_batch(stream, count=512, seed=0, reps=10):
 
 
 def measure_ladder(stream, flush, hbm_peak, sizes=((256, 3), (384, 3), (256, 2), (192, 4)), reps=5):
-    """Row a9 (size ladder past L2): one explicit step of the 3D heat problem
+    """Row a7 at more sizes (size ladder past L2): one explicit step of the 3D heat problem
     (PW, FP32 pairs, 1e-2 N(0,1) coefficients, dt = 0.05 h^2) at grids whose
     state (8 bytes per DOF as pairs) exceeds the 129 MB L2; L2 flushed before
     each step.  Reports DOF-updates/s and the step's algorithmic HBM rate
@@ -451,7 +451,7 @@ def measure_ladder(stream, flush, hbm_peak, sizes=((256, 3), (384, 3), (256, 2),
 
 
 def cpu_baseline_batch(res, sample=8):
-    """Oracle side of row a8: sampled instances' solutions against the oracle
+    """Oracle side of row f2: sampled instances' solutions against the oracle
     (backward error) and the oracle's sparse direct solve timed per instance."""
     import numpy as np
     from oracle import poisson_nd, systems
@@ -478,7 +478,7 @@ def cpu_baseline_batch(res, sample=8):
 
 
 def cpu_baseline_poisson(res):
-    """Oracle side of row a7: the backward error of the GPU solutions at full
+    """Oracle side of row f1: the backward error of the GPU solutions at full
     size (the oracle applies K by per-axis contractions; a sparse direct
     solve at 1M unknowns is out of reach here) and the oracle's sparse direct
     solve timed on a 256^2 sample."""
@@ -620,9 +620,9 @@ def run_native(args, rank, world):
     rows = measure_rows(c, u, dt, stream, flush, hbm_peak)
     rows['a4_source_table1'] = measure_source_table1(stream, flush, hbm_peak)
     poisson = measure_poisson(stream, flush)
-    rows['a7_poisson_2d_1024'] = cpu_baseline_poisson(poisson)
-    rows['a8_batch_poisson_512'] = cpu_baseline_batch(measure_batch(stream))
-    rows['a9_size_ladder'] = measure_ladder(stream, flush, hbm_peak)
+    rows['f1_poisson_2d_1024'] = cpu_baseline_poisson(poisson)
+    rows['f2_batch_poisson_512'] = cpu_baseline_batch(measure_batch(stream))
+    rows['a7_size_ladder'] = measure_ladder(stream, flush, hbm_peak)
     rows['hbm_peak_of_the_fracs'] = {'gbs': hbm_peak, 'source': src['hbm_source']}
     if rank == 0:
         # a failed comparison is reported in the line rather than ending the run
