@@ -54,3 +54,22 @@ def test_single_rank_defaults(monkeypatch):
         monkeypatch.delenv(k, raising=False)
     assert bench.dist_setup(1) == (0, 1)
     assert bench.max_over_ranks(3.0, 1) == 3.0
+
+
+def test_reference_arm_under_torchrun_prints_one_line():
+    """The reference arm launched as the driver launches it at N = 2 (torchrun,
+    127.0.0.1, gloo on a machine without GPUs): rank 0 alone runs the oracle
+    and prints one JSON line; the other rank exits 0 without work."""
+    import json
+    import subprocess
+    cmd = [sys.executable, '-m', 'torch.distributed.run', '--nnodes=1', '--nproc-per-node', '2',
+           '--master-addr', '127.0.0.1', '--master-port', str(_free_port()),
+           os.path.join(ROOT, 'bench.py'), '--impl', 'reference', '--gpus', '2', '--steps', '1', '--warmup', '0']
+    env = dict(os.environ, CUDA_VISIBLE_DEVICES='')
+    res = subprocess.run(cmd, cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    assert res.returncode == 0, res.stderr[-2000:]
+    lines = [l for l in res.stdout.splitlines() if l.startswith('{')]
+    assert len(lines) == 1, res.stdout
+    rec = json.loads(lines[0])
+    assert rec['impl'] == 'reference' and rec['n_gpus'] == 2 and rec['value'] > 0
+    assert rec['e2e']['h2d_bytes_per_step'] == 0 and rec['cpu_baseline']['kind'] == 'oracle'
