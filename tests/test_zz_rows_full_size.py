@@ -5,7 +5,10 @@ times, every coefficient against the oracle (rel-L2 <= 1e-5, FP32 pairs):
   elements, a tensor-product cubic sampled at each rule's points (PW: 2 points
   per piece, B-spline tests: 3 per element), FP32 samples, double-float sums;
 - the heat3d operator action T(u + dt Lap u) and the refined Kronecker mass
-  solve (Sec. 4.1-4.2): cubic C2, 128^3 elements, 4 points, PW tests."""
+  solve (Sec. 4.1-4.2): cubic C2, 128^3 elements, 4 points, PW tests;
+- one explicit step (Sec. 4.2, Eq. (6)) at the size-ladder grids past L2
+  (256^3 cubic and quadratic, 192^3 quartic; PW, 1e-2 N(0,1) coefficients,
+  dt = 0.05 h^2)."""
 import numpy as np
 import pytest
 
@@ -60,3 +63,21 @@ def test_heat3d_apply_and_solve_full_size():
     assert rel_l2(got_r, ref_r) < TOL['fp32r'], rel_l2(got_r, ref_r)
     ref_s = tensor.ads_solve(M, got_r)
     assert rel_l2(got_s, ref_s) < TOL['fp32r'], rel_l2(got_s, ref_s)
+
+
+@pytest.mark.parametrize('ne,p', [(256, 3), (256, 2), (192, 4)])
+def test_ladder_step_full_size(ne, p):
+    from paper_1910_08535_gb300 import workloads
+    from paper_1910_08535_gb300.igapw import Context
+    c = Context(dim=3, n_elem=ne, degree=p, nq=p + 1, test='pw', precision='fp32r')
+    u0 = workloads.normal_coeffs(c.shape, seed=ne)
+    dt = 0.05 / ne ** 2
+    u = c.from_numpy(u0)
+    c.step(u, dt, 1)
+    c.sync()
+    got = c.to_numpy(u)
+    c.close()
+    axes = [systems.Axis(ne, p, p + 1, 'pw') for _ in range(3)]
+    M, L = tensor.mass_mats(axes), tensor.lap_mats(axes)
+    ref = tensor.ads_solve(M, tensor.apply_heat_system(axes, u0, dt, M, L))
+    assert rel_l2(got, ref) < TOL['fp32r'], rel_l2(got, ref)
