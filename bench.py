@@ -15,6 +15,13 @@ With N > 1 (torchrun, one rank per GPU) every rank runs its own replica (the
 path has no exchange step across instances: weak scaling, no collective on the
 data path); the time is the max over ranks.  --impl reference times the FP64
 CPU oracle on the same workload (bounded sample per step).
+
+Besides the headline, the line carries `rows` keyed by the hot-path rows: a3
+operator action and a6 refined Kronecker solve (heat3d), a4 the Table 1
+source RHS (PW vs B-spline tests), f1 the 2D Poisson solve, f2 the
+512-instance batched Poisson solve, a7 the explicit step at grids past L2, a8
+the headline state's error against the FP64 oracle; and `serving`, the
+2000-request mixed stream (--no-serve skips it).
 """
 import argparse
 import json
