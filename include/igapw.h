@@ -140,7 +140,10 @@ typedef struct {
  * cuda_stream: a cudaStream_t (NULL = legacy default stream).
  * On success *out owns device memory until igapw_destroy.  Blocks until the
  * set-up kernels finish so that a singular factorization (IGAPW_ERR_SINGULAR,
- * linearly dependent tests, Sec. 2) is reported here. */
+ * linearly dependent tests, Sec. 2) is reported here.
+ * The context belongs to the CUDA device current at this call: every later
+ * call on it makes that device current for its duration and restores the
+ * caller's device before returning (cuda_stream must belong to that device). */
 int igapw_create(igapw_ctx** out, const igapw_desc* desc, void* cuda_stream);
 
 /* Replaces the knot vector of one axis by a caller-given open knot vector
@@ -195,9 +198,11 @@ int igapw_rhs_source(igapw_ctx* ctx, const void* f_dev, void* b_dev);
  *     8 * max(q_z q_y n_x, q_z n_y n_x) bytes (q_a = igapw_quad_points count);
  *     PW tests (one fused pass) and 1D need none.  Above half the array the
  *     call returns IGAPW_ERR_ARG with the sizes in igapw_last_error.
- *   - The first call on a device looks up the array's device address for the
- *     device current at that time (cudaGetSymbolAddress); make that first call
- *     before any stream capture.
+ *   - The array lives in a module of its own, which CUDA may load lazily (and
+ *     only then reserve the array): igapw_create looks its address up on the
+ *     context's device, so the array is in place before the first call, and
+ *     this entry point itself never causes that load.  Each call looks the
+ *     address up again on the context's device (a lookup, no allocation).
  *   - All calls on a device share the array and leave their intermediates in
  *     it; calls whose work overlaps on the GPU (different streams or contexts
  *     without ordering between them) race on it and must be serialised.
@@ -264,6 +269,21 @@ int igapw_solve(igapw_ctx* ctx, const void* r_dev, void* u_dev);
  * scratch tensors and waits for the context stream, so that call must not be
  * made inside a stream capture. */
 int igapw_step(igapw_ctx* ctx, double dt, int nsteps, void* u_dev);
+
+/* Launch shape of the split-form step kernel along one axis (a tuning
+ * control; no counterpart in the paper, which fixes no implementation).
+ * kind: 0 lines staged with the tables in shared memory (lines = x-lines or
+ * y/z columns per block, 32/16/8), 1 tables read from global memory (long
+ * lines), 2 staged tables with 16 columns, 3 the chunked kernel that keeps
+ * every line in registers in chunks of 17 rows (FP32_REFINE contexts whose
+ * lines have at most 544 rows; lines = 32, 16 or 8 lines per block).
+ * igapw_set_step_shape pins axis `axis` to (kind, lines); kind = -1 hands the
+ * axis back to the autotuner of the first igapw_step call.  A shape that
+ * cannot run on the context makes the next igapw_step fail with
+ * IGAPW_ERR_CUDA.  Pinning drops the captured step graphs.
+ * igapw_get_step_shape reports the shape in use (kind = -1: not tuned yet). */
+int igapw_set_step_shape(igapw_ctx* ctx, int axis, int kind, int lines);
+int igapw_get_step_shape(igapw_ctx* ctx, int axis, int* kind, int* lines);
 
 /* Same as igapw_step with HOST buffers: copies u_host (pinned memory gives an
  * asynchronous copy) into a context-owned device state, runs nsteps, copies

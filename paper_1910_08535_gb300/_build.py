@@ -12,7 +12,8 @@ CSRC = os.path.join(HERE, 'csrc')
 OBJ = os.path.join(HERE, '_objs')
 LIB = os.path.join(HERE, 'lib', 'libigapw.so')
 SOURCES = ['setup.cpp', 'tables.cu', 'solve.cu', 'rhs.cu', 'api.cu', 'noalloc.cu', 'step.cu', 'poisson.cu', 'batch.cu',
-           'step_f64_p2.cu', 'step_f64_p3.cu', 'step_f64_p4.cu', 'step_df_p2.cu', 'step_df_p3.cu', 'step_df_p4.cu']
+           'step_f64_p2.cu', 'step_f64_p3.cu', 'step_f64_p4.cu', 'step_df_p2.cu', 'step_df_p3.cu', 'step_df_p4.cu',
+           'chunkstep_p2.cu', 'chunkstep_p3.cu', 'chunkstep_p4.cu']
 ARCH = ['-gencode', 'arch=compute_103a,code=sm_103a']
 FLAGS = ['-O3', '-lineinfo', '-std=c++17', '-Xcompiler', '-fPIC', '--expt-relaxed-constexpr',
          '-Xcompiler', '-Wall', '-Xcompiler', '-Wno-unused-function']

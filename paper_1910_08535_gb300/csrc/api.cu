@@ -26,6 +26,11 @@ struct AxisMem {
            *PhiF = nullptr, *PhiB = nullptr;
     float *L32 = nullptr, *U32 = nullptr, *dinv32 = nullptr, *G32 = nullptr, *H32 = nullptr,
           *PhiF32 = nullptr, *PhiB32 = nullptr;
+    // chunked-step tables
+    double* ck_work = nullptr;
+    float4 *ck_cw = nullptr, *ck_aw = nullptr, *ck_fl = nullptr, *ck_fu = nullptr, *ck_fg = nullptr, *ck_fh = nullptr;
+    float *ck_fd = nullptr, *ck_psf = nullptr, *ck_psb = nullptr;
+    int* ck_J = nullptr;
 };
 
 struct GraphEntry {
@@ -39,6 +44,7 @@ struct GraphEntry {
 
 struct igapw_ctx {
     igapw_desc d{};
+    int device = 0;          // the CUDA device current at igapw_create; every call runs on it
     cudaStream_t stream = nullptr;
     cudaStream_t cap_stream = nullptr;
     int dim = 1, p = 2, W = 3, WQ = 1;
@@ -64,18 +70,43 @@ struct igapw_ctx {
     // split-step launch shapes per axis picked by timing (-1: not tuned yet)
     int step_cfg[3] = {-1, -1, -1};
     int step_nl[3] = {0, 0, 0};
+    bool step_pinned[3] = {false, false, false};
 };
 
 namespace {
 
 // FP64 multi-D Poisson: refinement corrections after the first FP32 solve
 constexpr int kPoissonRefineF64 = 3;
+// chunked explicit step: rows per chunk (the kernels' compile-time length) and
+// the most chunks a line may have (512 threads at 16 lines per block)
+constexpr int kChunkRows = 17;
+constexpr int kChunkMaxP = 32;
 
 int fail(igapw_ctx* c, int code, const std::string& msg) {
     if (c) c->err = msg;
     else g_create_error = msg;
     return code;
 }
+
+}  // namespace
+
+namespace igapw {
+
+// Makes `dev` the current device for the scope of an entry point and restores
+// the caller's device on return (a context's memory, streams and graphs
+// belong to the device it was created on).
+DeviceGuard::DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev_) == cudaSuccess && prev_ != dev) switched_ = cudaSetDevice(dev) == cudaSuccess;
+}
+DeviceGuard::~DeviceGuard() {
+    if (switched_) cudaSetDevice(prev_);
+}
+
+int ctx_device(const ::igapw_ctx* c) { return c->device; }
+
+}  // namespace igapw
+
+namespace {
 
 #define CKC(c, x)                                                                                   \
     do {                                                                                            \
@@ -117,6 +148,8 @@ void free_graphs(igapw_ctx* c) {
     for (auto& g : c->graphs) cudaGraphExecDestroy(g.exec);
     c->graphs.clear();
 }
+
+bool fp64(const igapw_ctx* c);
 
 // (Re)builds the device tables and factors of axis a from c->ax[a].
 int build_axis_device(igapw_ctx* c, int a) {
@@ -185,8 +218,34 @@ int build_axis_device(igapw_ctx* c, int a) {
     fa.PhiF32 = m.PhiF32; fa.PhiB32 = m.PhiB32;
     fa.status = c->status;
     // 2D/3D Poisson contexts solve by fast diagonalisation: no banded LU
-    if (!(c->d.op == IGAPW_OP_POISSON && c->dim >= 2)) launch_factor(fa, c->stream);
+    const bool banded = !(c->d.op == IGAPW_OP_POISSON && c->dim >= 2);
+    if (banded) launch_factor(fa, c->stream);
     CKC(c, cudaGetLastError());
+    // tables of the chunked explicit step (FP32-pair contexts with a mass matrix,
+    // lines of at most kChunkMaxP chunks)
+    int ckP = 0;
+    if (banded && !fp64(c) && c->d.op != IGAPW_OP_POISSON && p <= 4) {
+        ckP = (n + kChunkRows - 1) / kChunkRows;
+        if (ckP > kChunkMaxP) ckP = 0;
+    }
+    if (ckP > 0) {
+        const int q4 = (2 * W + 4) / 4;
+        CKC(c, dalloc(c, &m.ck_work, (size_t)2 * n * p));
+        CKC(c, dalloc(c, &m.ck_cw, (size_t)n * q4)); CKC(c, dalloc(c, &m.ck_aw, (size_t)n * q4));
+        CKC(c, dalloc(c, &m.ck_fl, (size_t)n)); CKC(c, dalloc(c, &m.ck_fu, (size_t)n));
+        CKC(c, dalloc(c, &m.ck_fg, (size_t)n)); CKC(c, dalloc(c, &m.ck_fh, (size_t)n));
+        CKC(c, dalloc(c, &m.ck_fd, (size_t)n));
+        CKC(c, dalloc(c, &m.ck_psf, (size_t)ckP * ckP * p * p)); CKC(c, dalloc(c, &m.ck_psb, (size_t)ckP * ckP * p * p));
+        CKC(c, dalloc(c, &m.ck_J, (size_t)1));
+        ChunkTableArgs ca{};
+        ca.n = n; ca.p = p; ca.W = W; ca.RS = kChunkRows; ca.P = ckP;
+        ca.L = m.L; ca.U = m.U; ca.dinv = m.dinv; ca.Adf = m.Adf; ca.Cdf = m.Cdf; ca.fstart = m.fstart;
+        ca.work = m.ck_work;
+        ca.cw = m.ck_cw; ca.aw = m.ck_aw; ca.fl = m.ck_fl; ca.fu = m.ck_fu; ca.fg = m.ck_fg; ca.fh = m.ck_fh;
+        ca.fd = m.ck_fd; ca.psf = m.ck_psf; ca.psb = m.ck_psb; ca.J = m.ck_J;
+        launch_chunk_tables(ca, c->stream);
+        CKC(c, cudaGetLastError());
+    }
 
     AxisDev& D = c->dev[a];
     D.n = n; D.nq = Q; D.wq = WQ;
@@ -202,6 +261,13 @@ int build_axis_device(igapw_ctx* c, int a) {
     D.ls64.PhiF = m.PhiF; D.ls64.PhiB = m.PhiB;
     D.ls32.L = m.L32; D.ls32.U = m.U32; D.ls32.dinv = m.dinv32; D.ls32.G = m.G32; D.ls32.H = m.H32;
     D.ls32.PhiF = m.PhiF32; D.ls32.PhiB = m.PhiB32;
+    D.ck = ChunkDev{};
+    if (ckP > 0) {
+        D.ck.rows = kChunkRows; D.ck.P = ckP;
+        D.ck.cw = m.ck_cw; D.ck.aw = m.ck_aw; D.ck.fl = m.ck_fl; D.ck.fu = m.ck_fu;
+        D.ck.fd = m.ck_fd; D.ck.fg = m.ck_fg; D.ck.fh = m.ck_fh;
+        D.ck.psf = m.ck_psf; D.ck.psb = m.ck_psb; D.ck.J = m.ck_J;
+    }
     return IGAPW_OK;
 }
 
@@ -325,7 +391,7 @@ int enqueue_steps(igapw_ctx* c, double dt, int nsteps, void* u, cudaStream_t st)
 // 32 / 16 / 8) on zeroed scratch tensors and keeps the fastest.  Runs once per
 // context, before the first step is captured.
 int tune_step(igapw_ctx* c, double dt) {
-    static const int cand[][2] = {{0, 32}, {0, 16}, {0, 8}, {2, 16}, {1, 32}, {1, 16}, {1, 8}};
+    static const int cand[][2] = {{3, 32}, {3, 16}, {3, 8}, {0, 32}, {0, 16}, {0, 8}, {2, 16}, {1, 32}, {1, 16}, {1, 8}};
     const size_t bytes = (size_t)c->ntot * 8;   // one pair or FP64 tensor
     unsigned char *tu = nullptr, *tacc = nullptr;
     CKC(c, cudaMallocAsync((void**)&tu, bytes, c->stream));
@@ -337,6 +403,7 @@ int tune_step(igapw_ctx* c, double dt) {
     CKC(c, cudaEventCreate(&e1));
     int rc = IGAPW_OK;
     for (int ax = 0; ax < c->dim && !rc; ++ax) {
+        if (c->step_pinned[ax]) continue;
         const int mode = c->dim == 1 ? 3 : (ax == 0 ? 0 : (ax == c->dim - 1 ? 2 : 1));
         float best = 1e30f;
         for (const auto& cd : cand) {
@@ -517,6 +584,7 @@ int igapw_create(igapw_ctx** out, const igapw_desc* desc, void* cuda_stream) {
     igapw_ctx* c = new (std::nothrow) igapw_ctx();
     if (!c) return fail(nullptr, IGAPW_ERR_OOM, "host allocation failed");
     c->d = *desc;
+    cudaGetDevice(&c->device);
     c->stream = (cudaStream_t)cuda_stream;
     c->dim = desc->dim;
     c->p = desc->degree;
@@ -535,6 +603,13 @@ int igapw_create(igapw_ctx** out, const igapw_desc* desc, void* cuda_stream) {
     }
     if (!rc) rc = setup_all(c, nullptr, -1);
     if (!rc) rc = alloc_scratch(c);
+    if (!rc) {
+        // place the static scratch of igapw_rhs_source_noalloc on this device now
+        // (its module is loaded on first use), so that entry point never has to
+        void* p = nullptr;
+        e = noalloc_scratch_address(&p);
+        if (e != cudaSuccess) rc = fail(c, IGAPW_ERR_CUDA, std::string("static scratch: ") + cudaGetErrorString(e));
+    }
     if (rc) {
         g_create_error = c->err;
         release(c);
@@ -548,6 +623,7 @@ int igapw_create(igapw_ctx** out, const igapw_desc* desc, void* cuda_stream) {
 
 int igapw_set_knots(igapw_ctx* c, int axis, const double* knots, int len) {
     if (!c) return fail(nullptr, IGAPW_ERR_ARG, "ctx is NULL");
+    DeviceGuard dg_(c->device);
     if (axis < 0 || axis >= c->dim || !knots || len <= 0) return fail(c, IGAPW_ERR_ARG, "bad axis or knots");
     CKC(c, cudaStreamSynchronize(c->stream));
     std::vector<double> kn(knots, knots + len);
@@ -561,7 +637,10 @@ int igapw_set_knots(igapw_ctx* c, int axis, const double* knots, int len) {
     keep[axis] = kn;
     free_graphs(c);
     release(c);
-    for (int a = 0; a < 3; ++a) c->step_cfg[a] = -1;   // launch shapes are re-tuned
+    for (int a = 0; a < 3; ++a) {   // launch shapes are re-tuned
+        c->step_cfg[a] = -1;
+        c->step_pinned[a] = false;
+    }
     CKC(c, dalloc(c, &c->status, 1));
     CKC(c, cudaMemsetAsync(c->status, 0, sizeof(unsigned), c->stream));
     int wmax = 0, wqmax = 0;
@@ -594,6 +673,7 @@ int igapw_set_knots(igapw_ctx* c, int axis, const double* knots, int len) {
 
 int igapw_quad_points(igapw_ctx* c, int axis, double* x, double* w, int* count) {
     if (!c) return fail(nullptr, IGAPW_ERR_ARG, "ctx is NULL");
+    DeviceGuard dg_(c->device);
     if (axis < 0 || axis >= c->dim || !count) return fail(c, IGAPW_ERR_ARG, "bad axis or count");
     const AxisSetup& s = c->ax[axis];
     *count = (int)s.qx.size();
@@ -604,6 +684,7 @@ int igapw_quad_points(igapw_ctx* c, int axis, double* x, double* w, int* count) 
 
 int igapw_basis_table(igapw_ctx* c, int axis, double* vals, int* first_fn) {
     if (!c) return fail(nullptr, IGAPW_ERR_ARG, "ctx is NULL");
+    DeviceGuard dg_(c->device);
     if (axis < 0 || axis >= c->dim) return fail(c, IGAPW_ERR_ARG, "bad axis");
     const AxisSetup& s = c->ax[axis];
     if (vals) {
@@ -617,6 +698,7 @@ int igapw_basis_table(igapw_ctx* c, int axis, double* vals, int* first_fn) {
 
 int igapw_rhs_source(igapw_ctx* c, const void* f_dev, void* b_dev) {
     if (!c) return fail(nullptr, IGAPW_ERR_ARG, "ctx is NULL");
+    DeviceGuard dg_(c->device);
     if (!f_dev || !b_dev) return fail(c, IGAPW_ERR_ARG, "NULL tensor");
     SourceArgs a{};
     a.dim = c->dim;
@@ -651,6 +733,7 @@ int igapw_rhs_source(igapw_ctx* c, const void* f_dev, void* b_dev) {
 
 int igapw_rhs_neumann(igapw_ctx* c, int axis, int side, const void* g_dev, void* b_dev) {
     if (!c) return fail(nullptr, IGAPW_ERR_ARG, "ctx is NULL");
+    DeviceGuard dg_(c->device);
     if (!g_dev || !b_dev) return fail(c, IGAPW_ERR_ARG, "NULL tensor");
     if (axis < 0 || axis >= c->dim || !((c->d.neumann_axes >> axis) & 1))
         return fail(c, IGAPW_ERR_ARG, "axis is not a Neumann axis of this context");
@@ -674,6 +757,7 @@ int igapw_rhs_neumann(igapw_ctx* c, int axis, int side, const void* g_dev, void*
 
 int igapw_apply(igapw_ctx* c, int op, double dt, const void* u_dev, void* r_dev) {
     if (!c) return fail(nullptr, IGAPW_ERR_ARG, "ctx is NULL");
+    DeviceGuard dg_(c->device);
     if (!u_dev || !r_dev) return fail(c, IGAPW_ERR_ARG, "NULL tensor");
     if (u_dev == r_dev) return fail(c, IGAPW_ERR_ARG, "u and r must not overlap");
     switch (op) {
@@ -700,6 +784,7 @@ int igapw_apply(igapw_ctx* c, int op, double dt, const void* u_dev, void* r_dev)
 
 int igapw_assemble_1d(igapw_ctx* c, int axis, int which, double* dense) {
     if (!c) return fail(nullptr, IGAPW_ERR_ARG, "ctx is NULL");
+    DeviceGuard dg_(c->device);
     if (axis < 0 || axis >= c->dim || !dense) return fail(c, IGAPW_ERR_ARG, "bad axis or output");
     const double* src = nullptr;
     if (which == IGAPW_OP_MASS) src = c->mem[axis].A;
@@ -721,6 +806,7 @@ int igapw_assemble_1d(igapw_ctx* c, int axis, int which, double* dense) {
 
 int igapw_solve(igapw_ctx* c, const void* r_dev, void* u_dev) {
     if (!c) return fail(nullptr, IGAPW_ERR_ARG, "ctx is NULL");
+    DeviceGuard dg_(c->device);
     if (!r_dev || !u_dev) return fail(c, IGAPW_ERR_ARG, "NULL tensor");
     if (c->fdm) {
         if (r_dev == u_dev) return fail(c, IGAPW_ERR_ARG, "the multi-D Poisson solve needs distinct r and u");
@@ -736,10 +822,13 @@ int igapw_solve(igapw_ctx* c, const void* r_dev, void* u_dev) {
 
 int igapw_step(igapw_ctx* c, double dt, int nsteps, void* u_dev) {
     if (!c) return fail(nullptr, IGAPW_ERR_ARG, "ctx is NULL");
+    DeviceGuard dg_(c->device);
     if (!u_dev || nsteps < 0) return fail(c, IGAPW_ERR_ARG, "bad arguments");
     if (c->d.op == IGAPW_OP_POISSON) return fail(c, IGAPW_ERR_ARG, "explicit steps need a mass-matrix context (op != POISSON)");
     if (nsteps == 0) return IGAPW_OK;
-    if (!(c->d.flags & IGAPW_FLAG_STEP_RHS_SOLVE) && c->step_cfg[0] < 0) {
+    bool untuned = false;
+    for (int a = 0; a < c->dim; ++a) untuned = untuned || c->step_cfg[a] < 0;
+    if (!(c->d.flags & IGAPW_FLAG_STEP_RHS_SOLVE) && untuned) {
         const int rc = tune_step(c, dt);
         if (rc) return rc;
     }
@@ -770,8 +859,31 @@ int igapw_step(igapw_ctx* c, double dt, int nsteps, void* u_dev) {
     return IGAPW_OK;
 }
 
+int igapw_set_step_shape(igapw_ctx* c, int axis, int kind, int lines) {
+    if (!c) return fail(nullptr, IGAPW_ERR_ARG, "ctx is NULL");
+    DeviceGuard dg_(c->device);
+    if (axis < 0 || axis >= c->dim) return fail(c, IGAPW_ERR_ARG, "axis out of range");
+    if (kind < -1 || kind > 3) return fail(c, IGAPW_ERR_ARG, "unknown step kernel kind");
+    if (kind >= 0 && (lines < 1 || lines > 32)) return fail(c, IGAPW_ERR_ARG, "lines per block must be 1..32");
+    free_graphs(c);
+    c->step_cfg[axis] = kind;
+    c->step_nl[axis] = kind >= 0 ? lines : 0;
+    c->step_pinned[axis] = kind >= 0;
+    return IGAPW_OK;
+}
+
+int igapw_get_step_shape(igapw_ctx* c, int axis, int* kind, int* lines) {
+    if (!c) return fail(nullptr, IGAPW_ERR_ARG, "ctx is NULL");
+    DeviceGuard dg_(c->device);
+    if (axis < 0 || axis >= c->dim || !kind || !lines) return fail(c, IGAPW_ERR_ARG, "bad arguments");
+    *kind = c->step_cfg[axis];
+    *lines = c->step_nl[axis];
+    return IGAPW_OK;
+}
+
 int igapw_step_host(igapw_ctx* c, double dt, int nsteps, void* u_host) {
     if (!c) return fail(nullptr, IGAPW_ERR_ARG, "ctx is NULL");
+    DeviceGuard dg_(c->device);
     if (!u_host) return fail(c, IGAPW_ERR_ARG, "NULL host buffer");
     const size_t bytes = fp64(c) ? (size_t)c->ntot * 8 : (size_t)c->ntot * 8;
     if (!c->state) {
@@ -789,6 +901,7 @@ int igapw_step_host(igapw_ctx* c, double dt, int nsteps, void* u_host) {
 
 int igapw_sync_status(igapw_ctx* c) {
     if (!c) return fail(nullptr, IGAPW_ERR_ARG, "ctx is NULL");
+    DeviceGuard dg_(c->device);
     cudaError_t e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return fail(c, IGAPW_ERR_CUDA, std::string("async error: ") + cudaGetErrorString(e));
     unsigned st = 0;
@@ -816,6 +929,7 @@ long long igapw_size(igapw_ctx* c, int* dims) {
 
 int igapw_destroy(igapw_ctx* c) {
     if (!c) return IGAPW_OK;
+    DeviceGuard dg_(c->device);
     cudaStreamSynchronize(c->stream);
     release(c);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);

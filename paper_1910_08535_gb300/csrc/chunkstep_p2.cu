@@ -1,0 +1,27 @@
+// Chunked explicit-step kernels (FP32-pair mode), degree 2.
+#include "chunkstep.cuh"
+
+namespace igapw {
+
+namespace {
+template <int W>
+cudaError_t pick_mode(const AxisStepArgs& a, int mode, cudaStream_t st) {
+    switch (mode) {
+        case 0: return run_chunk_step<2, W, 0, 17>(a, st);
+        case 1: return run_chunk_step<2, W, 1, 17>(a, st);
+        case 2: return run_chunk_step<2, W, 2, 17>(a, st);
+        case 3: return run_chunk_step<2, W, 3, 17>(a, st);
+    }
+    return cudaErrorInvalidValue;
+}
+}  // namespace
+
+cudaError_t launch_chunk_step_p2(const AxisStepArgs& a, int mode, cudaStream_t st) {
+    switch (a.W) {
+        case 3: return pick_mode<3>(a, mode, st);
+        case 5: return pick_mode<5>(a, mode, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace igapw

@@ -2,6 +2,7 @@
 // device descriptors, and the status word.
 #pragma once
 #include <cstdio>
+#include <cstring>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -117,6 +118,27 @@ struct LineSys {
     const T* PhiB;   // [5 * 32 * p * p] backward scan operators
 };
 
+// Packed FP32 tables of the chunked explicit step (chunkstep.cuh), built once
+// per axis by launch_chunk_tables from the FP64 factors.  A line of n rows is
+// cut into P chunks of `rows` rows (the last one holds the rest); chunk k's
+// partitioned solve takes the true tail of chunk k-1 as the local tail plus
+// the composed spike operators of up to J-1 earlier chunks (J = P unless the
+// operators decay below 1e-16 sooner).
+struct ChunkDev {
+    int rows;             // rows per chunk (the kernel's compile-time chunk length)
+    int P;                // chunks per line
+    const float4* cw;     // [n][nq4]: C window as (hi, lo) pairs, then fstart (int bits)
+    const float4* aw;     // [n][nq4]: A window, same layout
+    const float4* fl;     // [n]: l_{i,i-1} .. l_{i,i-p}
+    const float4* fu;     // [n]: u_{i,i+1} .. u_{i,i+p}; dinv in .w when p <= 3
+    const float* fd;      // [n]: 1 / u_{i,i}
+    const float4* fg;     // [n]: forward spike of row i (columns: the previous chunk's last p rows)
+    const float4* fh;     // [n]: backward spike (columns: the next chunk's first p rows)
+    const float* psf;     // [P][P][p][p]: psf[k][d] = Phi_{k-1} ... Phi_{k-d} (forward tails)
+    const float* psb;     // [P][P][p][p]: psb[k][d] = Theta_{k+1} ... Theta_{k+d} (backward heads)
+    const int* J;         // chunks that enter a composed tail or head (device scalar)
+};
+
 struct AxisDev {
     int n;          // coefficients on this axis
     int nq;         // quadrature points on this axis
@@ -131,6 +153,7 @@ struct AxisDev {
     TableSet TW;    // test weights over the point window [n * wq]
     LineSys<double> ls64;
     LineSys<float> ls32;
+    ChunkDev ck;    // chunked-step tables (ck.P == 0: not built)
 };
 
 // Status bits written by kernels (read back by igapw_sync_status).
@@ -162,6 +185,7 @@ namespace igapw {
 // many copies stay in flight without holding registers; cp_async_wait_all()
 // followed by __syncthreads() makes them visible to the block.
 // ---------------------------------------------------------------------------
+#ifndef IGAPW_HOST_EMU
 __device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
     const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
@@ -171,5 +195,15 @@ __device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+// the dynamic shared memory of a kernel
+#define IGAPW_DYNAMIC_SMEM(name) extern __shared__ __align__(16) unsigned char name[]
+#else
+// Host emulation of kernels (tests/c/cuda_emu.h): plain copies, and the
+// block's shared memory from the emulator.
+inline void cp_async4(void* smem, const void* gmem) { std::memcpy(smem, gmem, 4); }
+inline void cp_async8(void* smem, const void* gmem) { std::memcpy(smem, gmem, 8); }
+inline void cp_async_wait_all() {}
+#define IGAPW_DYNAMIC_SMEM(name) unsigned char* name = igapw_emu_smem()
+#endif
 
 }  // namespace igapw

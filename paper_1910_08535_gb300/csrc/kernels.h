@@ -40,6 +40,19 @@ struct FactorArgs {
     unsigned* status;
 };
 
+// Packed tables of the chunked step (chunkstep.cuh) from the FP64 factors.
+struct ChunkTableArgs {
+    int n, p, W, RS, P;
+    const double *L, *U, *dinv;   // factor_kernel output, [n][p] / [n]
+    const float2 *Adf, *Cdf;      // [n][W] double-float windows
+    const int* fstart;
+    double* work;                 // [2 n p]
+    float4 *cw, *aw, *fl, *fu, *fg, *fh;
+    float *fd, *psf, *psb;
+    int* J;
+};
+void launch_chunk_tables(const ChunkTableArgs& a, cudaStream_t st);
+
 void launch_basis_table(const double* t, int p, int Q, const double* qx, const int* qfirst,
                         double* vals, cudaStream_t st);
 void launch_fold(const FoldArgs& f, cudaStream_t st);
@@ -131,7 +144,8 @@ struct AxisStepArgs {
     int lines_per_block;    // lines staged per block: x-lines, or columns (a power of
                             // two <= 32) of y/z-lines (set by the launcher, or forced)
     int cfg;                // -1: the launcher's own choice; else forced with lines_per_block:
-                            // 0 staged tables, 1 tables in global memory, 2 staged 16 columns
+                            // 0 staged tables, 1 tables in global memory, 2 staged 16 columns,
+                            // 3 the chunked register kernel (FP32 pairs; 32, 16 or 8 lines)
     long long ntot;
     AxisDev ax;
     const void* u;
@@ -145,6 +159,21 @@ cudaError_t launch_axis_step(const AxisStepArgs& a, int mode, bool fp64, int p, 
 // ---- allocation-free source entry point (noalloc.cu <-> api.cu) ------------
 // Fills the source launch arguments of a context (work buffers left NULL) and
 // the bytes each of the two intermediates needs; records errors on the context.
+// Device address of the static scratch array of the allocation-free source
+// entry point on the current device (loads the module holding it if needed).
+cudaError_t noalloc_scratch_address(void** out);
+// Current-device scope for entry points, and the device a context belongs to.
+struct DeviceGuard {
+    explicit DeviceGuard(int dev);
+    ~DeviceGuard();
+    DeviceGuard(const DeviceGuard&) = delete;
+    DeviceGuard& operator=(const DeviceGuard&) = delete;
+
+private:
+    int prev_ = -1;
+    bool switched_ = false;
+};
+int ctx_device(const ::igapw_ctx* c);
 int source_setup(::igapw_ctx* c, const void* f_dev, void* b_dev, SourceArgs& a, size_t& need,
                  cudaStream_t& st, bool& f64);
 int record_error(::igapw_ctx* c, int code, const std::string& msg);

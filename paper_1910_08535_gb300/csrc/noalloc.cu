@@ -6,17 +6,20 @@
 // callers cannot let a library allocate at that point: hosts that reserve all
 // device memory up front and forbid later allocations, schedulers that admit
 // work against a fixed device-memory budget, and latency-critical loops that
-// cannot afford the wait.  This entry point takes
-// its intermediates from one statically sized device array instead and calls no
-// allocating routine.
+// cannot afford the wait.  This entry point takes its intermediates from one
+// statically sized device array instead and calls no allocating routine.
 //
 // The array is a file-scope __device__ variable: every GPU that loads the
 // library holds IGAPW_NOALLOC_SCRATCH_BYTES for it until the process exits.
-// Host code cannot use the symbol as a device address; the device address is
-// fetched once per device with cudaGetSymbolAddress (the device current at the
-// time of the call), on that device's first call of this entry point.
+// Host code cannot use the symbol as a device address.  Its device address
+// comes from cudaGetSymbolAddress with the context's device current.  This
+// translation unit has no kernels, so the array sits in a module of its own,
+// which lazy module loading would load (and so allocate) on the first address
+// query: igapw_create makes that query, so the array is in place before the
+// first call of this entry point.  Every call queries the address again (a
+// lookup once the module is loaded), so nothing is cached across
+// cudaDeviceReset or contexts.
 #include <cstdio>
-#include <mutex>
 
 #include "../../include/igapw.h"
 #include "kernels.h"
@@ -24,36 +27,22 @@
 namespace {
 
 constexpr size_t kScratchBytes = IGAPW_NOALLOC_SCRATCH_BYTES;
-constexpr int kMaxDevices = 64;
 
 // Shared by every call on a device; holds the previous call's intermediates.
 static __device__ __align__(256) unsigned char g_source_scratch[kScratchBytes];
 
-std::mutex g_mu;
-void* g_scratch_addr[kMaxDevices] = {};
-
-// Device address of g_source_scratch on the current device (set-up once per device).
-cudaError_t scratch_address(void** out) {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-    std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_scratch_addr[dev]) {
-        void* p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_source_scratch);
-        if (e != cudaSuccess) return e;
-        g_scratch_addr[dev] = p;
-    }
-    *out = g_scratch_addr[dev];
-    return cudaSuccess;
-}
-
 }  // namespace
+
+namespace igapw {
+
+cudaError_t noalloc_scratch_address(void** out) { return cudaGetSymbolAddress(out, g_source_scratch); }
+
+}  // namespace igapw
 
 extern "C" int igapw_rhs_source_noalloc(igapw_ctx* ctx, const void* f_dev, void* b_dev) {
     using namespace igapw;
     if (!ctx) return IGAPW_ERR_ARG;
+    DeviceGuard dg(ctx_device(ctx));
     if (!f_dev || !b_dev) return record_error(ctx, IGAPW_ERR_ARG, "NULL tensor");
     SourceArgs a;
     size_t need = 0;
@@ -71,7 +60,7 @@ extern "C" int igapw_rhs_source_noalloc(igapw_ctx* ctx, const void* f_dev, void*
         return record_error(ctx, IGAPW_ERR_ARG, msg);
     }
     void* base = nullptr;
-    cudaError_t e = scratch_address(&base);
+    cudaError_t e = noalloc_scratch_address(&base);
     if (e != cudaSuccess)
         return record_error(ctx, IGAPW_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
     // Both intermediates are written in full by the pass that produces them

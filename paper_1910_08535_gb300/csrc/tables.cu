@@ -3,6 +3,7 @@
 // the per-axis system matrices plus the data of the partitioned line solve.
 #include "common.cuh"
 #include "kernels.h"
+#include "chunktables.cuh"
 
 namespace igapw {
 
@@ -292,6 +293,8 @@ __global__ void factor_kernel(FactorArgs a) {
     for (int i = 0; i < n; ++i) a.dinv32[i] = (float)a.dinv[i];
     for (int i = 0; i < 5 * 32 * pp; ++i) { a.PhiF32[i] = (float)a.PhiF[i]; a.PhiB32[i] = (float)a.PhiB[i]; }
 }
+
+void launch_chunk_tables(const ChunkTableArgs& a, cudaStream_t st) { chunk_tables_kernel<<<1, 1, 0, st>>>(a); }
 
 void launch_basis_table(const double* t, int p, int Q, const double* qx, const int* qfirst,
                         double* vals, cudaStream_t st) {

@@ -56,6 +56,8 @@ _SIGS = {
     'igapw_solve': (_I, [_VP, _VP, _VP]),
     'igapw_step': (_I, [_VP, _D, _I, _VP]),
     'igapw_step_host': (_I, [_VP, _D, _I, _VP]),
+    'igapw_set_step_shape': (_I, [_VP, _I, _I, _I]),
+    'igapw_get_step_shape': (_I, [_VP, _I, ctypes.POINTER(_I), ctypes.POINTER(_I)]),
     'igapw_sync_status': (_I, [_VP]),
     'igapw_last_error': (ctypes.c_char_p, [_VP]),
     'igapw_size': (ctypes.c_longlong, [_VP, ctypes.POINTER(_I)]),
@@ -205,6 +207,16 @@ def igapw_step(ctx, dt, nsteps, u):
 
 def igapw_step_host(ctx, dt, nsteps, u_host):
     _check(load().igapw_step_host(ctx, float(dt), int(nsteps), _dptr(u_host)), ctx)
+
+
+def igapw_set_step_shape(ctx, axis, kind, lines):
+    _check(load().igapw_set_step_shape(ctx, int(axis), int(kind), int(lines)), ctx)
+
+
+def igapw_get_step_shape(ctx, axis):
+    kind, lines = ctypes.c_int(), ctypes.c_int()
+    _check(load().igapw_get_step_shape(ctx, int(axis), ctypes.byref(kind), ctypes.byref(lines)), ctx)
+    return kind.value, lines.value
 
 
 def igapw_sync_status(ctx):
@@ -362,6 +374,20 @@ class Context:
     def step(self, u, dt, nsteps):
         igapw_step(self.ctx, dt, nsteps, self._coefs(u, 'step: u'))
         return u
+
+    STEP_KINDS = {'staged': 0, 'global': 1, 'staged16': 2, 'chunked': 3}
+
+    def set_step_shape(self, axis, kind, lines=32):
+        """igapw_set_step_shape: pin the split-step kernel of one axis
+        ('staged', 'global', 'staged16', 'chunked', or None for the autotuner)."""
+        k = -1 if kind is None else self.STEP_KINDS[kind]
+        igapw_set_step_shape(self.ctx, axis, k, lines if k >= 0 else 0)
+
+    def get_step_shape(self, axis):
+        """(kind name or None, lines per block) in use on one axis."""
+        k, nl = igapw_get_step_shape(self.ctx, axis)
+        names = {v: n for n, v in self.STEP_KINDS.items()}
+        return names.get(k), nl
 
     def step_host(self, u_host, dt, nsteps):
         """igapw_step_host: `nsteps` steps of a HOST state (numpy array or CPU

@@ -17,6 +17,20 @@ def rel_l2(a, b):
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
 
 
+def max_abs_rel(a, b):
+    """Largest element-wise deviation relative to the largest reference entry."""
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+def rel_err(a, b):
+    """max(rel-L2, max-abs / max|ref|): parity is checked both norm-wise and
+    element-wise (a single wrong coefficient can hide in the L2 norm of a
+    large tensor but not in the element-wise bound)."""
+    return max(rel_l2(a, b), max_abs_rel(a, b))
+
+
 def max_abs(a, b):
     return float(np.max(np.abs(np.asarray(a, dtype=np.float64) - np.asarray(b, dtype=np.float64))))
 

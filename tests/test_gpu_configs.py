@@ -16,7 +16,7 @@ import numpy as np
 import pytest
 
 from oracle import heat
-from tests._cases import TOL, oracle_axes, rel_l2
+from tests._cases import TOL, oracle_axes, rel_err
 
 pytestmark = pytest.mark.gpu
 
@@ -52,7 +52,7 @@ def _run(name, test, prec, flags=0):
 @pytest.mark.parametrize('flags', [0, 2])
 def test_heat2d_full(test, prec, flags):
     got, ref = _run('heat2d', test, prec, flags)
-    err = rel_l2(got, ref)
+    err = rel_err(got, ref)
     print(f'heat2d {test} {prec} flags={flags}: rel-L2 {err:.3e} max-abs {np.abs(got - ref).max():.3e}')
     assert err < TOL[prec]
 
@@ -61,6 +61,6 @@ def test_heat2d_full(test, prec, flags):
 @pytest.mark.parametrize('flags', [0, 2, 3])
 def test_heat3d_full(test, flags):
     got, ref = _run('heat3d', test, 'fp32r', flags)
-    err = rel_l2(got, ref)
+    err = rel_err(got, ref)
     print(f'heat3d {test} flags={flags}: rel-L2 {err:.3e} max-abs {np.abs(got - ref).max():.3e}')
     assert err < TOL['fp32r']

@@ -7,7 +7,7 @@ import numpy as np
 import pytest
 
 from oracle import heat, tensor
-from tests._cases import TOL, oracle_axes, rel_l2
+from tests._cases import TOL, oracle_axes, rel_err
 
 pytestmark = pytest.mark.gpu
 
@@ -39,7 +39,7 @@ def test_heat_2d_1024_cubic(prec, test):
         got = c.to_numpy(ud)
         c.sync()
         c.close()
-        assert rel_l2(got, ref) < TOL[prec], (flags, rel_l2(got, ref))
+        assert rel_err(got, ref) < TOL[prec], (flags, rel_err(got, ref))
 
 
 @pytest.mark.parametrize('prec', ['fp64', 'fp32r'])
@@ -53,7 +53,7 @@ def test_mass_solve_2d_1024(prec):
     c.sync()
     c.close()
     ref = tensor.ads_solve(tensor.mass_mats(axes), r)
-    assert rel_l2(got, ref) < TOL[prec], rel_l2(got, ref)
+    assert rel_err(got, ref) < TOL[prec], rel_err(got, ref)
 
 
 @pytest.mark.parametrize('prec', ['fp64', 'fp32r'])
@@ -71,6 +71,6 @@ def test_long_1d_line(prec):
     sol = c.to_numpy(c.solve(c.from_numpy(u)))
     c.sync()
     c.close()
-    assert rel_l2(got, ref) < TOL[prec], rel_l2(got, ref)
+    assert rel_err(got, ref) < TOL[prec], rel_err(got, ref)
     ref_s = tensor.ads_solve(tensor.mass_mats(axes), u)
-    assert rel_l2(sol, ref_s) < TOL[prec], rel_l2(sol, ref_s)
+    assert rel_err(sol, ref_s) < TOL[prec], rel_err(sol, ref_s)

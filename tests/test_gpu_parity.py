@@ -6,7 +6,7 @@ import numpy as np
 import pytest
 
 from oracle import heat, poisson, systems, tensor
-from tests._cases import TOL, oracle_axes, rel_l2
+from tests._cases import TOL, oracle_axes, rel_err
 
 pytestmark = pytest.mark.gpu
 
@@ -53,19 +53,19 @@ def test_apply_solve_step(d, ne, p, test, prec):
         if beta:
             lap = tensor.apply_heat_system(axes, u, 1.0, M, L) - tensor.apply_heat_system(axes, u, 0.0, M, L)
             ref = ref + beta * lap
-        assert rel_l2(r, ref) < tol, (op, rel_l2(r, ref))
+        assert rel_err(r, ref) < tol, (op, rel_err(r, ref))
     # Kronecker mass solve
     rhs = workloads.uniform_coeffs(c.shape, seed=12)
     sol = c.to_numpy(c.solve(c.from_numpy(rhs)))
     ref = tensor.ads_solve(tensor.mass_mats(axes), rhs)
-    assert rel_l2(sol, ref) < tol, rel_l2(sol, ref)
+    assert rel_err(sol, ref) < tol, rel_err(sol, ref)
     # explicit steps (stable step size), split form and RHS-then-solve form
     h = 1.0 / (np.max(ne) if d > 1 else ne)
     dt = 0.05 * h * h / d
     ref = heat.run(axes, u, dt, 3)
     c.step(ud, dt, 3)
     got = c.to_numpy(ud)
-    assert rel_l2(got, ref) < tol, rel_l2(got, ref)
+    assert rel_err(got, ref) < tol, rel_err(got, ref)
     c.sync()
     c.close()
     from paper_1910_08535_gb300 import igapw
@@ -73,7 +73,7 @@ def test_apply_solve_step(d, ne, p, test, prec):
     ud2 = c2.from_numpy(u)
     c2.step(ud2, dt, 3)
     got2 = c2.to_numpy(ud2)
-    assert rel_l2(got2, ref) < tol, rel_l2(got2, ref)
+    assert rel_err(got2, ref) < tol, rel_err(got2, ref)
     c2.sync()
     c2.close()
 
@@ -95,7 +95,7 @@ def test_source_rhs(d, ne, test, prec, p, nq):
     b = c.to_numpy(c.rhs_source(fd))
     fin = f if prec == 'fp64' else f.astype(np.float32).astype(np.float64)
     ref = tensor.rhs_source(axes, fin)
-    assert rel_l2(b, ref) < TOL[prec] * (1 if prec == 'fp64' else 0.01), rel_l2(b, ref)
+    assert rel_err(b, ref) < TOL[prec] * (1 if prec == 'fp64' else 0.01), rel_err(b, ref)
 
 
 @pytest.mark.parametrize('test', ['pw', 'galerkin'])
@@ -113,13 +113,13 @@ def test_poisson_1d_config(test, prec):
     b = c.rhs_source(fd)
     u = c.to_numpy(c.solve(b))
     ref = poisson.solve(ax, workloads.sine_source)
-    assert rel_l2(u, ref) < TOL[prec], rel_l2(u, ref)
+    assert rel_err(u, ref) < TOL[prec], rel_err(u, ref)
     assert poisson.l2_error(ax, u, workloads.sine_exact) < (1e-6 if test == 'galerkin' else 2e-4)
     # apply(POISSON) then solve is the identity
     v = workloads.uniform_coeffs(c.shape, seed=3)
     v[0] = v[-1] = 0.0
     back = c.to_numpy(c.solve(c.apply('poisson', c.from_numpy(v))))
-    assert rel_l2(back, v) < TOL[prec]
+    assert rel_err(back, v) < TOL[prec]
 
 
 def test_status_flags_nonfinite():

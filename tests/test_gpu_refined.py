@@ -5,7 +5,7 @@ import numpy as np
 import pytest
 
 from oracle import heat, poisson_nd, systems, tensor
-from tests._cases import TOL, oracle_axes, rel_l2
+from tests._cases import TOL, oracle_axes, rel_err
 
 pytestmark = pytest.mark.gpu
 
@@ -34,16 +34,16 @@ def test_refined_apply_solve_step(d, ne, p, r, prec):
     ud = c.from_numpy(u)
     r_heat = c.to_numpy(c.apply('heat', ud, dt=0.01))
     ref = tensor.apply_heat_system(axes, u, 0.01)
-    assert rel_l2(r_heat, ref) < tol, rel_l2(r_heat, ref)
+    assert rel_err(r_heat, ref) < tol, rel_err(r_heat, ref)
     sol = c.to_numpy(c.solve(c.from_numpy(ref)))
     ref_s = tensor.ads_solve(tensor.mass_mats(axes), ref)
-    assert rel_l2(sol, ref_s) < tol, rel_l2(sol, ref_s)
+    assert rel_err(sol, ref_s) < tol, rel_err(sol, ref_s)
     h = 1.0 / (np.max(ne) if d > 1 else ne)
     dt = 0.05 * h * h / d
     c.step(ud, dt, 3)
     got = c.to_numpy(ud)
     ref = heat.run(axes, u, dt, 3)
-    assert rel_l2(got, ref) < tol, rel_l2(got, ref)
+    assert rel_err(got, ref) < tol, rel_err(got, ref)
     c.sync()
     c.close()
 
@@ -64,9 +64,9 @@ def test_refined_source_and_poisson_2d(prec):
     fd = torch.from_numpy(f.astype(np.float64 if prec == 'fp64' else np.float32)).cuda()
     b = c.rhs_source(fd)
     b_ref = poisson_nd.rhs(axes, f)
-    assert rel_l2(c.to_numpy(b), b_ref) < TOL[prec], rel_l2(c.to_numpy(b), b_ref)
+    assert rel_err(c.to_numpy(b), b_ref) < TOL[prec], rel_err(c.to_numpy(b), b_ref)
     sol = c.to_numpy(c.solve(b))
     ref = poisson_nd.solve(axes, b_ref)
-    assert rel_l2(sol, ref) < TOL[prec], rel_l2(sol, ref)
+    assert rel_err(sol, ref) < TOL[prec], rel_err(sol, ref)
     c.sync()
     c.close()

@@ -5,7 +5,7 @@ import numpy as np
 import pytest
 
 from oracle import heat, poisson_nd
-from tests._cases import TOL, oracle_axes, rel_l2
+from tests._cases import TOL, oracle_axes, rel_err
 
 pytestmark = pytest.mark.gpu
 
@@ -57,9 +57,9 @@ def test_mix_equals_alone_and_oracle():
         solo.check()
         solo.close()
         tol = TOL[req.shape.precision]
-        assert rel_l2(mixed[req.rid], one[req.rid]) <= tol, (req, rel_l2(mixed[req.rid], one[req.rid]))
+        assert rel_err(mixed[req.rid], one[req.rid]) <= tol, (req, rel_err(mixed[req.rid], one[req.rid]))
         ref = _oracle(req)
-        assert rel_l2(mixed[req.rid], ref) <= tol, (req, rel_l2(mixed[req.rid], ref))
+        assert rel_err(mixed[req.rid], ref) <= tol, (req, rel_err(mixed[req.rid], ref))
 
 
 def test_budget_caps_resident_slots():

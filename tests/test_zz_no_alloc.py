@@ -1,14 +1,15 @@
 """GPU test of igapw_rhs_source_noalloc, the allocation-free source RHS for
 callers that cannot let the library allocate device memory at call time (its
 intermediates live in a static device array instead of memory igapw_rhs_source
-allocates on first use).  Two calls in a row on different samples must each
-match the allocating entry point, and a problem whose intermediates exceed the
-static array must be rejected.  Collected last so that a failure here stops a
-run only after every other test has run; it also passes alone."""
+allocates on first use).  On a fresh context the first call must leave the
+device's free memory unchanged; two calls in a row on different samples must
+each match the allocating entry point; a problem whose intermediates exceed
+the static array must be rejected.  Collected last so that a failure here
+stops a run only after every other test has run; it also passes alone."""
 import numpy as np
 import pytest
 
-from tests._cases import TOL, rel_l2
+from tests._cases import TOL, rel_err
 
 pytestmark = pytest.mark.gpu
 
@@ -29,7 +30,33 @@ def _samples(c, dim, seed, dtype):
     return torch.from_numpy(f.astype(dtype)).cuda()
 
 
-@pytest.mark.parametrize('dim,ne', [(2, [37, 21]), (3, [13, 9, 11])])
+def test_noalloc_first_call_allocates_nothing():
+    import torch
+    from paper_1910_08535_gb300 import igapw
+    from paper_1910_08535_gb300.igapw import Context
+    # load the source kernels' module first (lazy module loading reserves
+    # device memory for code on a module's first launch)
+    w = Context(dim=3, n_elem=[13, 9, 11], degree=3, nq=4, test='galerkin', precision='fp32r')
+    w.rhs_source(_samples(w, 3, seed=1, dtype=np.float32))
+    w.sync()
+    w.close()
+    c = Context(dim=3, n_elem=[13, 9, 11], degree=3, nq=4, test='galerkin', precision='fp32r')
+    f = _samples(c, 3, seed=2, dtype=np.float32)
+    got = c.empty()
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    igapw.igapw_rhs_source_noalloc(c.ctx, f, got)
+    c.sync()
+    torch.cuda.synchronize()
+    free1 = torch.cuda.mem_get_info()[0]
+    assert free1 == free0, (free0, free1)
+    ref = c.rhs_source(f)
+    c.sync()
+    assert rel_err(c.to_numpy(got), c.to_numpy(ref)) <= TOL['fp32r']
+    c.close()
+
+
+@pytest.mark.parametrize('dim,ne', [(1, [53]), (2, [37, 21]), (3, [13, 9, 11])])
 @pytest.mark.parametrize('test', ['pw', 'galerkin'])
 @pytest.mark.parametrize('prec', ['fp64', 'fp32r'])
 def test_noalloc_matches_allocating_entry_point(dim, ne, test, prec):
@@ -43,7 +70,7 @@ def test_noalloc_matches_allocating_entry_point(dim, ne, test, prec):
         got = c.empty()
         igapw.igapw_rhs_source_noalloc(c.ctx, f, got)
         c.sync()
-        err = rel_l2(c.to_numpy(got), c.to_numpy(ref))
+        err = rel_err(c.to_numpy(got), c.to_numpy(ref))
         assert err <= TOL[prec], (call, err)
     c.close()
 
