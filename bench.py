@@ -16,12 +16,16 @@ path has no exchange step across instances: weak scaling, no collective on the
 data path); the time is the max over ranks.  --impl reference times the FP64
 CPU oracle on the same workload (bounded sample per step).
 
-Besides the headline, the line carries `rows` keyed by the hot-path rows: a3
-operator action and a6 refined Kronecker solve (heat3d), a4 the Table 1
-source RHS (PW vs B-spline tests), f1 the 2D Poisson solve, f2 the
-512-instance batched Poisson solve, a7 the explicit step at grids past L2, a8
-the headline state's error against the FP64 oracle; and `serving`, the
-2000-request mixed stream (--no-serve skips it).
+The line leads with the headline, the HBM roofline of one explicit step (16
+bytes per coefficient and step: read u, write u', FP32 pairs) and the step
+kernels in use; `rows` (keyed by the hot-path rows) follow: a4 the Table 1
+source RHS (PW vs B-spline tests), a3 operator action and a6 refined
+Kronecker solve (heat3d), a7 the heat2d workload and the size ladder past
+L2 (3D and 2D, PW and Galerkin), a8 the error of every output against the
+FP64 oracle (rel-L2, max-abs, max-abs relative to the largest entry; heat
+states after steps 1, 10 and the last), f1 the 2D Poisson solve, f2 the
+512-instance batched Poisson solve; then `serving`, the 2000-request mixed
+stream (--no-serve skips it; --no-ladder skips the size ladder).
 """
 import argparse
 import json
@@ -45,6 +49,7 @@ def parse():
     ap.add_argument('--impl', default='native', choices=['native', 'reference'])
     ap.add_argument('--residual', default='df', choices=['fp64', 'df'])
     ap.add_argument('--no-serve', action='store_true', help='skip the request-stream measurement')
+    ap.add_argument('--no-ladder', action='store_true', help='skip the size ladder')
     return ap.parse_args()
 
 
@@ -162,9 +167,52 @@ def peak_sources(pk):
             'clock_source': 'measured' if 'sm_max_mhz' in pk else 'nominal (2070 MHz)'}
 
 
+def rnd(x, sig=4):
+    """Rounds floats (recursively) to `sig` significant digits for a compact line."""
+    import math
+    if isinstance(x, float):
+        if x == 0.0 or not math.isfinite(x):
+            return x
+        return float(f'{x:.{sig}g}')
+    if isinstance(x, dict):
+        return {k: rnd(v, sig) for k, v in x.items()}
+    if isinstance(x, (list, tuple)):
+        return [rnd(v, sig) for v in x]
+    return x
+
+
+def errors(got, ref):
+    """rel-L2, max-abs and max-abs relative to the largest reference entry."""
+    import numpy as np
+    got = np.asarray(got, dtype=np.float64)
+    ref = np.asarray(ref, dtype=np.float64)
+    d = np.abs(got - ref)
+    return {'rel_l2': float(np.linalg.norm(got - ref) / max(np.linalg.norm(ref), 1e-300)),
+            'max_abs': float(d.max()), 'max_abs_rel': float(d.max() / max(np.abs(ref).max(), 1e-300))}
+
+
+def oracle_heat(name, test, snaps, seed=0):
+    """FP64 oracle run of a heat workload: the states after the steps listed
+    in `snaps` (ascending), and the CPU seconds it took."""
+    from oracle import systems, tensor
+    from paper_1910_08535_gb300 import workloads
+    w = workloads.WORKLOADS[name]
+    axes = [systems.Axis(w['n_elem'], w['degree'], w['nq'], test) for _ in range(w['dim'])]
+    M, L = tensor.mass_mats(axes), tensor.lap_mats(axes)
+    u = workloads.initial_state(name, seed=seed)
+    dt = workloads.dt_of(name)
+    out = {}
+    t0 = time.perf_counter()
+    for s in range(1, max(snaps) + 1):
+        u = tensor.ads_solve(M, tensor.apply_heat_system(axes, u, dt, M, L))
+        if s in snaps:
+            out[s] = u.copy()
+    return out, time.perf_counter() - t0
+
+
 def cpu_baseline_oracle(test='pw', steps=20):
     """The FP64 oracle on the same workload: `steps` explicit steps at full size."""
-    import numpy as np
+    import numpy as np  # noqa: F401
     from oracle import systems, tensor
     from paper_1910_08535_gb300 import workloads
     w = workloads.WORKLOADS[WORKLOAD]
@@ -184,29 +232,6 @@ def cpu_baseline_oracle(test='pw', steps=20):
     return {'value': u.size * steps / el, 'unit': 'DOF-updates/s', 'cores': cores, 'kind': 'oracle',
             'sample': f'{steps} of the 50 explicit steps of heat3d at full size (131^3), FP64 numpy, PW tests',
             'seconds': el}
-
-
-def cpu_baseline_heat_parity(got, steps, seed=0):
-    """Precision of the headline output, with the oracle's run timed on the
-    host cores: the FP64 oracle takes the same heat3d workload (initial state,
-    dt, `steps` steps, PW tests) and the GPU result `got` (float64 array of
-    the final coefficients) is compared with it: rel-L2, max-abs and max-abs
-    relative to the largest coefficient."""
-    import numpy as np
-    from oracle import systems, tensor
-    from paper_1910_08535_gb300 import workloads
-    w = workloads.WORKLOADS[WORKLOAD]
-    axes = [systems.Axis(w['n_elem'], w['degree'], w['nq'], 'pw') for _ in range(3)]
-    M, L = tensor.mass_mats(axes), tensor.lap_mats(axes)
-    u = workloads.initial_state(WORKLOAD, seed=seed)
-    dt = workloads.dt_of(WORKLOAD)
-    t0 = time.perf_counter()
-    for _ in range(steps):
-        u = tensor.ads_solve(M, tensor.apply_heat_system(axes, u, dt, M, L))
-    el = time.perf_counter() - t0
-    d = got - u
-    return {'rel_l2': float(np.linalg.norm(d) / np.linalg.norm(u)), 'max_abs': float(np.max(np.abs(d))),
-            'max_abs_rel': float(np.max(np.abs(d)) / np.max(np.abs(u))), 'oracle_cpu_s': el}
 
 
 def run_reference(args, rank, world):
@@ -250,54 +275,70 @@ def _time_events(stream, fn, reps, flush=None, warm=3):
     return sum(out) / len(out)
 
 
-def cpu_baseline_rows(dt):
-    """CPU-baseline leg of rows a3 / a6: the oracle's operator action and
-    Kronecker solve on the same heat3d state, timed on the host cores."""
+def source_sha(files):
+    """Short hash of library sources (ties a stored ncu figure to the code it measured)."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in files:
+        with open(os.path.join(ROOT, f), 'rb') as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+STEP_SOURCES = ('paper_1910_08535_gb300/csrc/chunkstep.cuh', 'paper_1910_08535_gb300/csrc/chunkstep_p3.cu',
+                'paper_1910_08535_gb300/csrc/common.cuh')
+TRAFFIC_PROFILE = 'profiles/chunk_step_kernel_heat3d.md'
+
+
+def profiled_traffic():
+    """DRAM bytes of one explicit step (three chunk_step_kernel launches) from
+    the ncu summary under profiles/ (a line `traffic_bytes_per_step: B
+    source_sha: S`), or None if there is none or the step kernel's sources
+    changed since it was taken."""
+    try:
+        txt = open(os.path.join(ROOT, TRAFFIC_PROFILE)).read()
+    except OSError:
+        return None, 'no ncu summary'
+    import re
+    m = re.search(r'traffic_bytes_per_step:\s*([0-9.eE+]+)\s+source_sha:\s*([0-9a-f]+)', txt)
+    if not m:
+        return None, 'no traffic line in the ncu summary'
+    if m.group(2) != source_sha(STEP_SOURCES):
+        return None, 'step kernel changed since the ncu capture'
+    return float(m.group(1)), TRAFFIC_PROFILE
+
+
+def measure_rows(ctx, u, dt, stream, flush, hbm_peak):
+    """Rows a3 (operator action) and a6 (refined Kronecker solve) on heat3d:
+    device time per call, the algorithmic HBM fraction (read u, write r: 16
+    bytes per coefficient), and the error of each output against the oracle
+    (same input, timed on the host cores)."""
     from oracle import systems, tensor
     from paper_1910_08535_gb300 import workloads
+    n = ctx.ntot
+    r = ctx.empty()
+    out = ctx.empty()
+    t_apply = _time_events(stream, lambda: ctx.apply('heat', u, dt, out=r), 10, flush)
+    t_solve = _time_events(stream, lambda: ctx.solve(r, out=out), 10, flush)
+    ctx.sync()
+    uin, rr, ss = ctx.to_numpy(u), ctx.to_numpy(r), ctx.to_numpy(out)
     w = workloads.WORKLOADS[WORKLOAD]
     axes = [systems.Axis(w['n_elem'], w['degree'], w['nq'], 'pw') for _ in range(3)]
     M, L = tensor.mass_mats(axes), tensor.lap_mats(axes)
-    u0 = workloads.initial_state(WORKLOAD)
     t0 = time.perf_counter()
-    rr = tensor.apply_heat_system(axes, u0, dt, M, L)
+    ref_r = tensor.apply_heat_system(axes, uin, dt, M, L)
     t1 = time.perf_counter()
-    tensor.ads_solve(M, rr)
+    ref_s = tensor.ads_solve(M, rr)
     t2 = time.perf_counter()
-    return t1 - t0, t2 - t1
-
-
-def measure_rows(ctx_pw, u, dt, stream, flush, hbm_peak):
-    """Rows a3 (operator action) and a6 (refined Kronecker solve) on heat3d:
-    device time per call, bytes per DOF moved by the algorithm, and the
-    oracle's CPU time for the same operation."""
-    n = ctx_pw.ntot
-    r = ctx_pw.empty()
-    out = ctx_pw.empty()
-    t_apply = _time_events(stream, lambda: ctx_pw.apply('heat', u, dt, out=r), 10, flush)
-    t_solve = _time_events(stream, lambda: ctx_pw.solve(r, out=out), 10, flush)
-    cpu_apply, cpu_solve = cpu_baseline_rows(dt)
     return {
         'a3_apply_heat': {'us': t_apply * 1e6, 'dof_per_s': n / t_apply,
                           'hbm_frac_16B_per_dof': 16.0 * n / t_apply / 1e9 / hbm_peak,
                           'kernel': 'contract_kernel (7 double-float banded passes)',
-                          'oracle_cpu_s': cpu_apply},
+                          'vs_oracle': errors(rr, ref_r), 'oracle_cpu_s': t1 - t0},
         'a6_solve_refined': {'us': t_solve * 1e6, 'dof_per_s': n / t_solve,
                              'kernels': '3 FP32 line solves + double-float residual + 3 line solves',
-                             'oracle_cpu_s': cpu_solve},
+                             'vs_oracle': errors(ss, ref_s), 'oracle_cpu_s': t2 - t1},
     }
-
-
-def cpu_baseline_source(ne, p, nq, test, f, got):
-    """CPU-baseline leg of row a4: the oracle's source RHS from the same
-    samples, timed on the host cores, and the GPU result's rel-L2 against it."""
-    import numpy as np
-    from oracle import systems, tensor
-    axes = [systems.Axis(ne, p, nq, test) for _ in range(3)]
-    t0 = time.perf_counter()
-    ref = tensor.rhs_source(axes, f.astype(np.float64))
-    tcpu = time.perf_counter() - t0
-    return float(np.linalg.norm(got - ref) / np.linalg.norm(ref)), tcpu
 
 
 def measure_source_table1(stream, flush, hbm_peak, reps=5):
@@ -308,6 +349,7 @@ def measure_source_table1(stream, flush, hbm_peak, reps=5):
     rule's points (FP32), the RHS accumulates in double-float."""
     import numpy as np
     import torch
+    from oracle import systems, tensor
     from paper_1910_08535_gb300 import workloads
     from paper_1910_08535_gb300.igapw import Context
     ne, p = 128, 2
@@ -323,20 +365,95 @@ def measure_source_table1(stream, flush, hbm_peak, reps=5):
             t = _time_events(stream, lambda: c.rhs_source(f, out=b), reps, flush)
             c.sync()
         q = [len(x) for x in pts]
-        fbytes = 4 * q[0] * q[1] * q[2]
-        alg = fbytes + 8 * c.ntot
-        err, tcpu = cpu_baseline_source(ne, p, nq, test, f.cpu().numpy(), c.to_numpy(b))
-        res[test] = {'nq': nq, 'points': q[0] * q[1] * q[2], 'us': t * 1e6, 'dof_per_s': c.ntot / t,
-                     'alg_bytes': alg, 'achieved_gbs': alg / t / 1e9, 'hbm_frac': alg / t / 1e9 / hbm_peak,
-                     'rel_l2_vs_oracle': err, 'oracle_cpu_s': tcpu}
+        alg = 4 * q[0] * q[1] * q[2] + 8 * c.ntot
+        axes = [systems.Axis(ne, p, nq, test) for _ in range(3)]
+        t0 = time.perf_counter()
+        ref = tensor.rhs_source(axes, f.cpu().numpy().astype(np.float64))
+        tcpu = time.perf_counter() - t0
+        res[test] = {'us': t * 1e6, 'hbm_frac': alg / t / 1e9 / hbm_peak, 'achieved_gbs': alg / t / 1e9,
+                     'nq': nq, 'points': q[0] * q[1] * q[2], 'dof_per_s': c.ntot / t, 'alg_bytes': alg,
+                     'vs_oracle': errors(c.to_numpy(b), ref), 'oracle_cpu_s': tcpu}
         c.close()
         del f, b
     res['pw_speedup_over_galerkin'] = res['galerkin']['us'] / res['pw']['us']
     return res
 
 
+def measure_heat(name, test, stream, flush, steps_timed, reps=3):
+    """A heat workload on the device: DOF-updates/s over full runs (L2
+    flushed before each), and the states after steps 1, 10 and the last,
+    each against the FP64 oracle."""
+    import torch
+    from paper_1910_08535_gb300 import workloads
+    from paper_1910_08535_gb300.igapw import Context
+    w = workloads.WORKLOADS[name]
+    dt = workloads.dt_of(name)
+    u0 = workloads.initial_state(name)
+    with torch.cuda.stream(stream):
+        c = Context(dim=w['dim'], n_elem=w['n_elem'], degree=w['degree'], nq=w['nq'], test=test,
+                    precision='fp32r', stream=stream)
+        init = c.from_numpy(u0)
+        u = c.empty()
+
+        def run():
+            u.copy_(init)
+            c.step(u, dt, steps_timed)
+        t = _time_events(stream, run, reps, flush, warm=2)
+        snaps = sorted({1, 10, w['steps']})
+        u.copy_(init)
+        got, done = {}, 0
+        for s in snaps:
+            c.step(u, dt, s - done)
+            done = s
+            c.sync()
+            got[s] = c.to_numpy(u)
+        shapes = [c.get_step_shape(a) for a in range(w['dim'])]
+        c.close()
+    ref, tcpu = oracle_heat(name, test, snaps)
+    return {'dof_updates_per_s': (init.numel() // 2) * steps_timed / t, 'run_us': t * 1e6, 'steps': steps_timed,
+            'step_kernels': [f'{k}/{nl}' for k, nl in shapes],
+            'vs_oracle': {f'step_{s}': errors(got[s], ref[s]) for s in snaps}, 'oracle_cpu_s': tcpu}
+
+
+LADDER_3D = ((128, 3), (192, 3), (256, 2), (256, 3), (256, 4), (384, 3), (512, 2), (512, 3))
+LADDER_2D = ((1024, 3), (2048, 3), (4096, 3), (8192, 3))
+
+
+def measure_ladder(stream, flush, hbm_peak, reps=5):
+    """Size ladder of the explicit step (the a7 row past L2): one step of the
+    3D and 2D heat problem (FP32 pairs, 1e-2 N(0,1) coefficients, dt = 0.05
+    h^2), PW and Galerkin tests on the same grids, L2 flushed before each
+    step.  Reports DOF-updates/s, the step's algorithmic HBM rate (read u,
+    write u': 16 bytes per coefficient) and the PW / Galerkin ratio."""
+    import torch
+    from paper_1910_08535_gb300 import workloads
+    from paper_1910_08535_gb300.igapw import Context
+    out = []
+    for dim, sizes in ((3, LADDER_3D), (2, LADDER_2D)):
+        for ne, p in sizes:
+            row = {'dim': dim, 'n_elem': ne, 'degree': p}
+            for test in ('pw', 'galerkin'):
+                with torch.cuda.stream(stream):
+                    c = Context(dim=dim, n_elem=ne, degree=p, nq=p + 1, test=test, precision='fp32r', stream=stream)
+                    u = c.from_numpy(workloads.normal_coeffs(c.shape, seed=ne))
+                    dt = 0.05 / ne ** 2
+                    t = _time_events(stream, lambda: c.step(u, dt, 1), reps, flush)
+                    c.sync()
+                    shapes = [c.get_step_shape(a) for a in range(dim)]
+                row['dof'] = c.ntot
+                row[test] = {'step_us': t * 1e6, 'dof_updates_per_s': c.ntot / t,
+                             'alg_hbm_frac': 16 * c.ntot / t / 1e9 / hbm_peak,
+                             'kernels': '/'.join(f'{k}{nl}' for k, nl in shapes)}
+                c.close()
+                del u
+                torch.cuda.empty_cache()
+            row['pw_over_galerkin'] = row['pw']['dof_updates_per_s'] / row['galerkin']['dof_updates_per_s']
+            out.append(row)
+    return out
+
+
 def measure_poisson(stream, flush, reps=10):
-    """Row a7 (multi-D Poisson, Sec. 4.3 problem): 2D, 1024^2 elements, cubic
+    """Row f1 (multi-D Poisson, Sec. 4.3 problem): 2D, 1024^2 elements, cubic
     PW tests, solve K u = b by fast diagonalisation (FP32 GEMM transforms per
     axis) inside iterative refinement; FP32 pairs (1 correction) and FP64 (3
     corrections), plain FP32 GEMMs and BF16x9 tensor-pipe emulation.  The
@@ -368,6 +485,20 @@ def measure_poisson(stream, flush, reps=10):
                                     'fdm_applications': applications, 'create_s': t_create,
                                     'solution': c.to_numpy(u), 'rhs': c.to_numpy(b)}
             c.close()
+    # the solution against the oracle's sparse direct solve on a 256^2 sample
+    from oracle import poisson_nd, systems
+    small = {}
+    for prec in ('fp32r', 'fp64'):
+        c = Context(dim=2, n_elem=256, degree=p, nq=p + 1, test='pw', precision=prec, op='poisson', bc='dirichlet0')
+        bh = np.random.default_rng(0).standard_normal(c.shape)
+        got = c.to_numpy(c.solve(c.from_numpy(bh)))
+        c.sync()
+        c.close()
+        axes = [systems.Axis(256, p, p + 1, 'pw', 'dirichlet0') for _ in range(2)]
+        t0 = time.perf_counter()
+        ref = poisson_nd.solve(axes, bh, sparse=True)
+        small[prec] = dict(errors(got, ref), oracle_sparse_direct_s=time.perf_counter() - t0)
+    res['sample_256x256_vs_oracle'] = small
     return res
 
 
@@ -376,8 +507,11 @@ def measure_serving(requests=2000, seed=6, budget=120 * 10 ** 9):
     64^2..1024^2 / 30% 3D 32^3..160^3, p in {2,3}, FP64 / FP32 pairs) through
     the continuous-batching server: slots for every shape created first
     (resident tables, factors and pencils), capacity from a closed-loop run of
-    300 requests, then `requests` Poisson arrivals at 80% of that capacity."""
+    300 requests, then `requests` Poisson arrivals at 80% of that capacity.
+    A sample of the served results is checked against the oracle."""
+    import numpy as np
     import torch
+    from oracle import heat, poisson_nd, systems
     from paper_1910_08535_gb300 import serve
     torch.cuda.empty_cache()        # the rows before leave cached blocks of other sizes
     srv = serve.Server(budget_bytes=budget)
@@ -392,12 +526,35 @@ def measure_serving(requests=2000, seed=6, budget=120 * 10 ** 9):
     cap = serve.summarize(recs)['throughput_req_s']
     rate = 0.8 * cap
     stream = serve.make_stream(requests, rate=rate, seed=seed)
-    recs, _ = srv.run(stream)
+    recs, results = srv.run(stream, keep_results=True)
     srv.check()
     out = serve.summarize(recs)
+    # precision of served results: the smallest requests of each kind and precision
+    worst = {}
+    byid = {r.rid: r for r in stream}
+    for kind in ('heat', 'poisson'):
+        for prec in ('fp32r', 'fp64'):
+            cand = sorted((r for r in stream if r.shape.kind == kind and r.shape.precision == prec),
+                          key=lambda r: r.shape.ntot)[:3]
+            errs = []
+            for r in cand:
+                sh = r.shape
+                axes = [systems.Axis(sh.n_elem, sh.degree, sh.nq, sh.test,
+                                     'dirichlet0' if kind == 'poisson' else 'none') for _ in range(sh.dim)]
+                if kind == 'heat':
+                    ref = heat.run(axes, serve.base_state(sh), r.dt_h2 / (sh.n_elem ** 2 * sh.dim), r.steps)
+                else:
+                    from paper_1910_08535_gb300 import workloads
+                    pts = [axes[a].points()[0] for a in range(sh.dim)]
+                    f = workloads.sine_product_source(pts, r.k)
+                    from oracle import tensor
+                    ref = poisson_nd.solve(axes, tensor.rhs_source(axes, f), sparse=True)
+                errs.append(errors(results[byid[r.rid].rid], ref))
+            if errs:
+                worst[f'{kind}_{prec}'] = {k: max(e[k] for e in errs) for k in errs[0]}
     out.update({'capacity_req_s': cap, 'arrival_rate_req_s': rate, 'budget_bytes': budget,
                 'resident_bytes': srv.used, 'slots': sum(len(v) for v in srv.pools.values()),
-                'warm_s': t_warm, 'evicted': srv.evicted,
+                'warm_s': t_warm, 'evicted': srv.evicted, 'served_vs_oracle_worst_of_3': worst,
                 'mix': '70% 2D (64..1024)^2 / 30% 3D (32..160)^3 on 16-rung geometric ladders, p in {2,3}, '
                        'Poisson solve / 20-step heat 50/50, FP64 / FP32 pairs 50/50, PW tests'})
     srv.close()
@@ -405,7 +562,7 @@ def measure_serving(requests=2000, seed=6, budget=120 * 10 ** 9):
 
 
 def measure_batch(stream, count=512, seed=0, reps=10):
-    """Row a8 (batched 2D Poisson, 512 uneven instances): N log-uniform on 16
+    """Row f2 (batched 2D Poisson, 512 uneven instances): N log-uniform on 16
     rungs in [32, 512] per axis, p in {2, 3}, PW tests, FP32 pairs with one
     refinement; manufactured sources amp sin(k1 pi x) sin(k2 pi y), k uniform in
     1..4.  Times the fused source kernel and the graph-captured batch solve."""
@@ -428,81 +585,71 @@ def measure_batch(stream, count=512, seed=0, reps=10):
     out = {'instances': count, 'dof': dof, 'create_s': t_create, 'tiles_source_residual': bt.tiles(),
            'source_us': t_src * 1e6, 'solve_us': t_solve * 1e6, 'instances_per_s': count / t_solve,
            'dof_per_s': dof / t_solve, 'gemm_tflops': flops / t_solve / 1e12,
-           'shapes_sample': shapes[:4], 'params': par, 'batch': bt}
-    return out
-
-
-def measure_ladder(stream, flush, hbm_peak, sizes=((256, 3), (384, 3), (256, 2), (192, 4)), reps=5):
-    """Row a7 at more sizes (size ladder past L2): one explicit step of the 3D heat problem
-    (PW, FP32 pairs, 1e-2 N(0,1) coefficients, dt = 0.05 h^2) at grids whose
-    state (8 bytes per DOF as pairs) exceeds the 129 MB L2; L2 flushed before
-    each step.  Reports DOF-updates/s and the step's algorithmic HBM rate
-    (read u, write u': 16 bytes per DOF)."""
-    import torch
-    from paper_1910_08535_gb300 import workloads
-    from paper_1910_08535_gb300.igapw import Context
-    out = []
-    for ne, p in sizes:
-        with torch.cuda.stream(stream):
-            c = Context(dim=3, n_elem=ne, degree=p, nq=p + 1, test='pw', precision='fp32r', stream=stream)
-            u = c.from_numpy(workloads.normal_coeffs(c.shape, seed=ne))
-            dt = 0.05 / ne ** 2
-            t = _time_events(stream, lambda: c.step(u, dt, 1), reps, flush)
-            c.sync()
-        out.append({'n_elem': ne, 'degree': p, 'dof': c.ntot, 'state_mb': 8 * c.ntot / 1e6, 'step_us': t * 1e6,
-                    'dof_updates_per_s': c.ntot / t, 'alg_hbm_gbs': 16 * c.ntot / t / 1e9,
-                    'alg_hbm_frac': 16 * c.ntot / t / 1e9 / hbm_peak})
-        c.close()
-        del u
+           'params': par, 'batch': bt}
     return out
 
 
 def cpu_baseline_batch(res, sample=8):
     """Oracle side of row f2: sampled instances' solutions against the oracle
-    (backward error) and the oracle's sparse direct solve timed per instance."""
+    (backward error, and the error against the oracle's sparse direct solve
+    of the same right-hand side) and that solve timed per instance."""
     import numpy as np
     from oracle import poisson_nd, systems
     from paper_1910_08535_gb300 import workloads
     bt, par = res.pop('batch'), res.pop('params')
     shapes = workloads.batch_shapes(res['instances'], seed=0)
     idx = np.random.Generator(np.random.PCG64(1)).choice(len(shapes), size=sample, replace=False)
-    etas, secs = [], []
+    etas, secs, errs = [], [], []
     for i in idx:
         nx, ny, p = shapes[i]
         axes = [systems.Axis(nx, p, p + 1, 'pw', 'dirichlet0'), systems.Axis(ny, p, p + 1, 'pw', 'dirichlet0')]
         b = bt.to_numpy(int(i), 0)
-        etas.append(poisson_nd.backward_error(axes, bt.to_numpy(int(i), 1), b))
+        u = bt.to_numpy(int(i), 1)
+        etas.append(poisson_nd.backward_error(axes, u, b))
         if nx <= 200:        # the sparse direct solve of the largest grids takes minutes
             t0 = time.perf_counter()
-            poisson_nd.solve(axes, b, sparse=True)
+            ref = poisson_nd.solve(axes, b, sparse=True)
             secs.append((time.perf_counter() - t0, (nx + p) * (ny + p)))
+            errs.append(errors(u, ref))
     bt.close()
     res['max_backward_error_sample'] = float(max(etas))
+    if errs:
+        res['vs_oracle_worst_sample'] = {k: max(e[k] for e in errs) for k in errs[0]}
     res['oracle_sparse_direct_dof_per_s_sample'] = (float(sum(d for _, d in secs) / sum(t for t, _ in secs))
                                                     if secs else None)
-    res['oracle_sample'] = f'{sample} random instances of the batch (sparse direct timing on those with N <= 200)'
+    res['oracle_sample'] = f'{sample} random instances of the batch (sparse direct on those with N <= 200)'
     return res
 
 
 def cpu_baseline_poisson(res):
     """Oracle side of row f1: the backward error of the GPU solutions at full
     size (the oracle applies K by per-axis contractions; a sparse direct
-    solve at 1M unknowns is out of reach here) and the oracle's sparse direct
-    solve timed on a 256^2 sample."""
-    import numpy as np
+    solve at 1M unknowns is out of reach here)."""
     from oracle import poisson_nd, systems
     ne, p = 1024, 3
     axes = [systems.Axis(ne, p, p + 1, 'pw', 'dirichlet0') for _ in range(2)]
     out = {}
     for k, v in res.items():
+        if k == 'sample_256x256_vs_oracle':
+            out[k] = v
+            continue
         out[k] = {kk: vv for kk, vv in v.items() if kk not in ('solution', 'rhs')}
         out[k]['backward_error_vs_oracle'] = poisson_nd.backward_error(axes, v['solution'], v['rhs'])
-    small = [systems.Axis(256, p, p + 1, 'pw', 'dirichlet0') for _ in range(2)]
-    b = np.random.default_rng(0).standard_normal((259, 259))
-    t0 = time.perf_counter()
-    poisson_nd.solve(small, b, sparse=True)
-    out['oracle_sparse_direct_256x256_s'] = time.perf_counter() - t0
     return out
+
+
+def window_width(ne, p, nq, test):
+    """Padded window width (3, 5, 7 or 9) of the 1D tested mass and Laplacian
+    rows: the number of coefficients a row of the step's banded passes reads."""
+    import numpy as np
+    from oracle import systems
+    ax = systems.Axis(ne, p, nq, test)
+    span = 0
+    for M in (systems.mass(ax), systems.laplace(ax)):
+        for row in M:
+            nz = np.nonzero(row)[0]
+            span = max(span, int(nz[-1] - nz[0] + 1))
+    return next(x for x in (3, 5, 7, 9) if x >= span)
 
 
 def run_native(args, rank, world):
@@ -555,15 +702,17 @@ def run_native(args, rank, world):
     c, init, u, t_pw, clocks = run_test('pw')
     ntot = c.ntot
     value = world * ntot * nsteps * args.steps / t_pw
+    step_kernels = [c.get_step_shape(a) for a in range(3)]
     # Galerkin comparator on the same mesh
     cg, _, _, t_g, _ = run_test('galerkin')
     value_g = world * ntot * nsteps * args.steps / t_g
+    g_kernels = [cg.get_step_shape(a) for a in range(3)]
     cg.close()
 
-    # dominant kernels: the three per-axis step launches (axis_step_kernel),
-    # timed as one explicit step (a one-step graph) on the context stream with
-    # L2 flushed before each; the work is double-float arithmetic on the FP32
-    # pipes, so the roofline is the FP32 issue rate (ALU-bound).
+    # dominant kernel: the explicit step, three per-axis launches of the step
+    # kernel, timed as one step (a one-step graph) with CUDA events on the
+    # context stream, L2 flushed before each.  Algorithmic bytes per step:
+    # read u and write u' as FP32 pairs, 16 bytes per coefficient.
     one = []
     with torch.cuda.stream(stream):
         for i in range(23):
@@ -579,32 +728,33 @@ def run_native(args, rank, world):
                 one.append(e0.elapsed_time(e1) / 1e3)
     t_one = sum(one) / len(one)
     pk = peaks()
-    # FP32 operations per DOF and axis of the double-float split step (FMA = 1):
-    # g = C u, W compensated products of 12 operations + 3 to normalise;
-    # residual g - A w0, W products of 11 + 3; two FP32 banded solves of
-    # 2p + 1 = 7 each; update two-sum 6 + compensated product 12 + 3.
-    W, p = 5, 3                             # PW cubic window (Galerkin: 7)
-    ops_per_dof_axis = 12 * W + 3 + 11 * W + 3 + 2 * (2 * p + 1) + 21
-    alg_ops = ntot * 3 * ops_per_dof_axis   # one step = 3 axis launches
     src = peak_sources(pk)
-    sm_mhz = src['sm_max_mhz']
-    alu_peak = 152 * 128 * sm_mhz * 1e6 / 1e12
-    achieved = alg_ops / t_one / 1e12
-    # DRAM bytes of one step (3 launches, x staged 32 lines, y/z staged 16 columns) from
-    # one ncu capture of `python -m paper_1910_08535_gb300.profile_cases heat3d-step`
-    # (dram__bytes_read.sum + dram__bytes_write.sum, cold-cache replay)
-    step_traffic = 90.3e6
-    roof = {'bound': 'alu', 'achieved': achieved, 'peak': alu_peak, 'unit': 'TFLOP/s', 'frac': achieved / alu_peak,
-            'traffic': step_traffic, 'traffic_note': 'bytes per step (3 launches), ncu cold-cache replay',
-            'kernel': 'axis_step_kernel<DF,3,5,*> x3 (one explicit step, PW)',
-            'peak_kind': f'derived: 152 SMs x 128 FP32 lanes x {sm_mhz:.0f} MHz (FP32 operations/s, FMA = 1)',
-            'clock_source': src['clock_source'],
-            'alg_ops_per_step': alg_ops, 'step_us': t_one * 1e6}
     hbm_peak = src['hbm_gbs']
-    hbm_view = {'alg_bytes_per_dof_step': 16, 'achieved_gbs': 16.0 * ntot / t_one / 1e9, 'peak_gbs': hbm_peak,
-                'peak_source': src['hbm_source'],
-                'frac': 16.0 * ntot / t_one / 1e9 / hbm_peak,
-                'note': 'state is L2-resident across the 50 steps of a run; the step is ALU-bound (double-float)'}
+    alg_bytes = 16.0 * ntot
+    traffic, traffic_src = profiled_traffic()
+    # ALU view (explanation, not the headline): FP32 operations per coefficient
+    # and axis of the double-float step with the window width W and degree p
+    # of the context: g = C u (W compensated products of 12 + 3), residual
+    # g - A w0 (W of 11 + 2), two FP32 banded solves with spike corrections
+    # (4p + 1 each), update 15; the method's own FP32 work is the banded
+    # passes alone: 2 W (C, A) + 2 (2p + 1) flops.
+    Wc, p = window_width(w['n_elem'], w['degree'], w['nq'], 'pw'), w['degree']
+    emu_ops = 3 * ((12 * Wc + 3) + (11 * Wc + 2) + 2 * (4 * p + 1) + 15)
+    method_flops = 3 * (2 * Wc + 2 * (2 * p + 1))
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    alu_peak_ops = sms * 128 * src['sm_max_mhz'] * 1e6
+    roof = {'bound': 'hbm', 'achieved': alg_bytes / t_one / 1e9, 'peak': hbm_peak, 'unit': 'GB/s',
+            'frac': alg_bytes / t_one / 1e9 / hbm_peak, 'traffic': traffic,
+            'traffic_source': traffic_src,
+            'kernel': 'chunk_step_kernel x3 per explicit step (x, y, z lines), heat3d PW',
+            'alg_bytes_per_step': alg_bytes, 'step_us': t_one * 1e6, 'peak_source': src['hbm_source'],
+            'note': 'heat3d state (18 MB) is L2-resident within a step; past-L2 grids in rows.a7_size_ladder',
+            'alu_view': {'fp32_ops_per_dof_step_double_float': emu_ops,
+                         'method_flops_per_dof_step': method_flops,
+                         'ops_per_s': ntot * emu_ops / t_one,
+                         'peak_ops_per_s': alu_peak_ops,
+                         'frac': ntot * emu_ops / t_one / alu_peak_ops,
+                         'peak_kind': f'{sms} SMs x 128 FP32 lanes x {src["sm_max_mhz"]:.0f} MHz'}}
 
     # end to end through the public C ABI with host buffers (pinned)
     host = torch.empty((2,) + c.shape, dtype=torch.float32).pin_memory()
@@ -619,26 +769,24 @@ def run_native(args, rank, world):
         if i >= args.warmup:
             e2e_t.append(el)
     e2e_total = max_over_ranks(sum(e2e_t), world)
-    # the pinned buffer now holds the state after the last end-to-end run
-    final_state = hb[0].astype(np.float64) + hb[1].astype(np.float64)
     e2e = {'value': world * ntot * nsteps * args.steps / e2e_total, 'unit': 'DOF-updates/s',
            'h2d_bytes_per_step': 8 * ntot, 'd2h_bytes_per_step': 8 * ntot}
 
-    rows = measure_rows(c, u, dt, stream, flush, hbm_peak)
+    rows = {}
     rows['a4_source_table1'] = measure_source_table1(stream, flush, hbm_peak)
-    poisson = measure_poisson(stream, flush)
-    rows['f1_poisson_2d_1024'] = cpu_baseline_poisson(poisson)
-    rows['f2_batch_poisson_512'] = cpu_baseline_batch(measure_batch(stream))
-    rows['a7_size_ladder'] = measure_ladder(stream, flush, hbm_peak)
-    rows['hbm_peak_of_the_fracs'] = {'gbs': hbm_peak, 'source': src['hbm_source']}
+    rows.update(measure_rows(c, u, dt, stream, flush, hbm_peak))
+    c.close()
     if rank == 0:
-        # a failed comparison is reported in the line rather than ending the run
-        try:
-            prec = cpu_baseline_heat_parity(final_state, nsteps, seed=rank)
-        except Exception as ex:
-            prec = {'error': repr(ex)}
-        prec['output'] = f'heat3d PW state after {nsteps} steps (FP32 pairs, through igapw_step_host) vs the FP64 oracle'
-        rows['a8_precision_heat3d'] = prec
+        rows['a8_heat3d_pw'] = measure_heat('heat3d', 'pw', stream, flush, nsteps)
+        rows['a8_heat3d_galerkin'] = measure_heat('heat3d', 'galerkin', stream, flush, nsteps)
+    rows['a7_heat2d_pw'] = measure_heat('heat2d', 'pw', stream, flush, 200)
+    rows['a7_heat2d_galerkin'] = measure_heat('heat2d', 'galerkin', stream, flush, 200)
+    rows['a7_heat2d_pw_over_galerkin'] = (rows['a7_heat2d_pw']['dof_updates_per_s'] /
+                                          rows['a7_heat2d_galerkin']['dof_updates_per_s'])
+    if not args.no_ladder:
+        rows['a7_size_ladder'] = measure_ladder(stream, flush, hbm_peak)
+    rows['f1_poisson_2d_1024'] = cpu_baseline_poisson(measure_poisson(stream, flush))
+    rows['f2_batch_poisson_512'] = cpu_baseline_batch(measure_batch(stream))
     # the request server is a one-GPU process: measured at N = 1
     serving = measure_serving() if (world == 1 and not args.no_serve) else None
 
@@ -654,15 +802,18 @@ def run_native(args, rank, world):
             'data': 'synthetic (seeded PCG64; coefficients 1e-2 N(0,1))',
             'config': {'workload': 'heat3d: 3D explicit heat, cubic C2, 128^3 elements (2,248,091 DOF), '
                                    '4x4x4 Gauss, dt=0.05h^2, 50 steps per bench step, PW tests',
-                       'l2': 'flushed (512 MB write) before every timed step', 'residual': args.residual},
-            'galerkin': {'value': value_g, 'unit': 'DOF-updates/s', 'pw_over_galerkin': value / value_g},
-            'roofline': roof, 'hbm_view': hbm_view, 'clocks': clocks, 'e2e': e2e, 'rows': rows,
-            'serving': serving,
+                       'l2': 'flushed (512 MB write) before every timed step', 'residual': args.residual,
+                       'step_kernels': [f'{k}/{nl}' for k, nl in step_kernels]},
+            'roofline': roof,
+            'galerkin': {'value': value_g, 'unit': 'DOF-updates/s', 'pw_over_galerkin': value / value_g,
+                         'step_kernels': [f'{k}/{nl}' for k, nl in g_kernels],
+                         'note': 'split form: both tests reduce to banded per-axis tables (PW width 5, '
+                                 'Galerkin 7); the PW advantage is the narrower table'},
+            'clocks': clocks, 'e2e': e2e,
             'gpu_launches': launches_per_time_step * nsteps * args.steps,
-            'cpu_baseline': cpu}
+            'cpu_baseline': cpu, 'rows': rows, 'serving': serving}
     if rank == 0:
-        print(json.dumps(line))
-    c.close()
+        print(json.dumps(rnd(line)))
 
 
 def main():

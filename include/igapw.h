@@ -183,6 +183,19 @@ int igapw_basis_table(igapw_ctx* ctx, int axis, double* vals, int* first_fn);
  * float hi/lo pair planes).  Dirichlet rows get b = 0. Asynchronous. */
 int igapw_rhs_source(igapw_ctx* ctx, const void* f_dev, void* b_dev);
 
+/* Source RHS of the separable source f(x) = amp * prod_a sin(k[a] pi x_a)
+ * [Sec. 4.1 generation of the right-hand side, for a source known in closed
+ * form]: b = T f over the context's quadrature points, with the source
+ * evaluated on the device (FP64 sinpi) instead of sampled by the caller.
+ * Because the tests are tensor products, b = amp (x)_a v_a with the 1D sums
+ * v_a[i] = sum_q T_a,i(x_q) w_q sin(k[a] pi x_q) over the axis' points
+ * (v in FP64, b written as FP64 or FP32 pairs per precision; Dirichlet rows
+ * b = 0).  With amp = pi^2 sum_a k[a]^2 it is the source of the manufactured
+ * solution u = prod_a sin(k[a] pi x_a) of -Lap u = f.  k: host array of dim
+ * doubles.  b_dev: caller-owned device tensor.  Asynchronous; allocates
+ * nothing (the context holds the 1D factors). */
+int igapw_rhs_source_sine(igapw_ctx* ctx, double amp, const double* k, void* b_dev);
+
 /* Allocation-free variant of igapw_rhs_source (the paper has no counterpart:
  * this is a deployment aid).  igapw_rhs_source allocates the two intermediate
  * tensors of its axis-by-axis passes on its first call for a context (a

@@ -32,9 +32,40 @@ def _extra():
     return os.environ.get('IGAPW_NVCC_EXTRA', '').split()
 
 
+def _obj(src):
+    return os.path.join(OBJ, os.path.splitext(src)[0] + '.o')
+
+
+def _deps(src):
+    """Files the object of `src` depends on (from the .d file nvcc wrote with
+    it), or None when unknown."""
+    d = os.path.splitext(_obj(src))[0] + '.d'
+    try:
+        txt = open(d).read().replace('\\\n', ' ')
+    except OSError:
+        return None
+    parts = txt.split(':', 1)
+    return [f for f in parts[1].split() if f] if len(parts) == 2 else None
+
+
+def _stale(src):
+    out = _obj(src)
+    if not os.path.exists(out):
+        return True
+    deps = _deps(src)
+    if deps is None:
+        return True
+    t = os.path.getmtime(out)
+    try:
+        return any(os.path.getmtime(f) > t for f in deps + [os.path.join(CSRC, src)])
+    except OSError:
+        return True
+
+
 def _compile(src):
-    out = os.path.join(OBJ, os.path.splitext(src)[0] + '.o')
-    cmd = [nvcc(), *ARCH, *FLAGS, *_extra(), '-c', os.path.join(CSRC, src), '-o', out]
+    out = _obj(src)
+    dep = os.path.splitext(out)[0] + '.d'
+    cmd = [nvcc(), *ARCH, *FLAGS, *_extra(), '-MD', '-MF', dep, '-c', os.path.join(CSRC, src), '-o', out]
     r = subprocess.run(cmd, capture_output=True, text=True)
     return src, r.returncode, r.stdout + r.stderr, out
 
@@ -51,15 +82,18 @@ def build(verbose=False, force=False):
             return LIB
     os.makedirs(OBJ, exist_ok=True)
     os.makedirs(os.path.dirname(LIB), exist_ok=True)
-    with concurrent.futures.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
-        results = list(ex.map(_compile, SOURCES))
+    # only the units whose object is older than the unit or a header it
+    # includes are recompiled (all of them with force)
+    todo = [s for s in SOURCES if force or _stale(s)]
+    with concurrent.futures.ThreadPoolExecutor(max_workers=max(1, len(todo))) as ex:
+        results = list(ex.map(_compile, todo))
     failed = [r for r in results if r[1] != 0]
     for src, rc, log, _ in results:
         if verbose or rc != 0:
             sys.stderr.write(f'--- {src} (rc={rc})\n{log}')
     if failed:
         raise RuntimeError('nvcc failed for ' + ', '.join(f[0] for f in failed))
-    objs = [r[3] for r in results]
+    objs = [_obj(s) for s in SOURCES]
     tmp = LIB + '.tmp'
     libdir = os.path.join(os.path.dirname(os.path.dirname(os.path.realpath(nvcc()))), 'lib64')
     cmd = [nvcc(), *ARCH, '-shared', '-o', tmp, *objs, '-lcudart', '-lcublas', '-lcusolver',

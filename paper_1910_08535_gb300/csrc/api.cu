@@ -60,6 +60,7 @@ struct igapw_ctx {
     float* u0 = nullptr;     // FP32 first solve [ntot]
     float* rho = nullptr;    // FP32 residual [ntot]
     void* state = nullptr;   // igapw_step_host device state
+    double* sine_v[3] = {nullptr, nullptr, nullptr};   // rhs_source_sine 1D factors
     void* src0 = nullptr;    // rhs_source intermediates
     void* src1 = nullptr;
     size_t src_bytes = 0;
@@ -230,11 +231,12 @@ int build_axis_device(igapw_ctx* c, int a) {
     }
     if (ckP > 0) {
         const int q4 = (2 * W + 4) / 4;
-        CKC(c, dalloc(c, &m.ck_work, (size_t)2 * n * p));
-        CKC(c, dalloc(c, &m.ck_cw, (size_t)n * q4)); CKC(c, dalloc(c, &m.ck_aw, (size_t)n * q4));
-        CKC(c, dalloc(c, &m.ck_fl, (size_t)n)); CKC(c, dalloc(c, &m.ck_fu, (size_t)n));
-        CKC(c, dalloc(c, &m.ck_fg, (size_t)n)); CKC(c, dalloc(c, &m.ck_fh, (size_t)n));
-        CKC(c, dalloc(c, &m.ck_fd, (size_t)n));
+        const size_t np = (size_t)ckP * kChunkRows;   // padded line
+        CKC(c, dalloc(c, &m.ck_work, 2 * np * p));
+        CKC(c, dalloc(c, &m.ck_cw, np * q4)); CKC(c, dalloc(c, &m.ck_aw, np * q4));
+        CKC(c, dalloc(c, &m.ck_fl, np)); CKC(c, dalloc(c, &m.ck_fu, np));
+        CKC(c, dalloc(c, &m.ck_fg, np)); CKC(c, dalloc(c, &m.ck_fh, np));
+        CKC(c, dalloc(c, &m.ck_fd, np));
         CKC(c, dalloc(c, &m.ck_psf, (size_t)ckP * ckP * p * p)); CKC(c, dalloc(c, &m.ck_psb, (size_t)ckP * ckP * p * p));
         CKC(c, dalloc(c, &m.ck_J, (size_t)1));
         ChunkTableArgs ca{};
@@ -490,6 +492,13 @@ int valid_desc(const igapw_desc* d, std::string& why) {
 
 int alloc_scratch(igapw_ctx* c) {
     const size_t nt = (size_t)c->ntot;
+    for (int a = 0; a < 3; ++a) {
+        if (a < c->dim) {
+            CKC(c, dalloc(c, &c->sine_v[a], (size_t)c->n[a]));
+        } else {   // an absent axis enters the separable source as the factor 1
+            CKC(c, upload(c, &c->sine_v[a], std::vector<double>{1.0}));
+        }
+    }
     if (fp64(c)) {
         CKC(c, dalloc(c, (double**)&c->r, nt));
         CKC(c, dalloc(c, (double**)&c->w, nt));
@@ -728,6 +737,28 @@ int igapw_rhs_source(igapw_ctx* c, const void* f_dev, void* b_dev) {
     a.ntot = c->ntot;
     cudaError_t e = launch_source(a, fp64(c), c->stream);
     if (e != cudaSuccess) return fail(c, IGAPW_ERR_CUDA, std::string("source: ") + cudaGetErrorString(e));
+    return IGAPW_OK;
+}
+
+int igapw_rhs_source_sine(igapw_ctx* c, double amp, const double* k, void* b_dev) {
+    if (!c) return fail(nullptr, IGAPW_ERR_ARG, "ctx is NULL");
+    DeviceGuard dg_(c->device);
+    if (!k || !b_dev) return fail(c, IGAPW_ERR_ARG, "NULL argument");
+    SineSourceArgs a{};
+    a.dim = c->dim;
+    for (int d = 0; d < 3; ++d) {
+        a.n[d] = c->n[d];
+        a.q[d] = d < c->dim ? (int)c->ax[d].qx.size() : 1;
+        a.ax[d] = c->dev[d];
+        a.qx[d] = d < c->dim ? c->mem[d].qx : nullptr;
+        a.k[d] = d < c->dim ? k[d] : 0.0;
+        a.v[d] = c->sine_v[d];
+    }
+    a.amp = amp;
+    a.out = b_dev;
+    a.ntot = c->ntot;
+    cudaError_t e = launch_source_sine(a, fp64(c), c->stream);
+    if (e != cudaSuccess) return fail(c, IGAPW_ERR_CUDA, std::string("sine source: ") + cudaGetErrorString(e));
     return IGAPW_OK;
 }
 

@@ -17,8 +17,10 @@
 //
 // Work layout.  A block holds NL lines (a power of two: lane l of a line
 // group) and P chunks per line; thread (l, k) owns rows [k R, k R + R) of
-// line l (R = the compile-time chunk length, the last chunk holds the rest),
-// keeps g, the forward and the backward iterates of those rows in registers,
+// line l (R = the compile-time chunk length; lines are padded to P R rows
+// with decoupled identity rows, so every chunk is full and the unrolled row
+// loops carry no guards), keeps g, the forward and the backward iterates of
+// those rows in registers,
 // and exchanges only p chunk-boundary values per solve direction through
 // shared memory.  The partitioned solve: each chunk solves with a zero tail,
 // the true tail of the previous chunk is the sum of the local tails of the
@@ -38,12 +40,13 @@ namespace chunkstep {
 
 __host__ __device__ constexpr int nq4(int W) { return (2 * W + 4) / 4; }
 
-// shared memory of one block (bytes), shared by kernel and launcher
-__host__ __device__ inline size_t smem_bytes(bool xl, int n, int W, int NL, int P, int KP) {
-    const int nr = n + W;
+// shared memory of one block (bytes), shared by kernel and launcher; np = the
+// padded line length P * rows
+__host__ __device__ inline size_t smem_bytes(bool xl, int np, int W, int NL, int P, int KP) {
+    const int nr = np + W;
     // must match the carve-up in chunk_step_kernel: y/z tiles use a row stride of 32
     const size_t cap = xl ? (size_t)NL * (nr | 1) : (size_t)nr * 32;
-    return cap * 8 + cap * 4 + (size_t)2 * P * KP * NL * 4;
+    return cap * 8 + cap * 8 + cap * 4 + (size_t)2 * P * KP * NL * 4;
 }
 
 // Loads v[0..KP) of a float4 table row.
@@ -68,11 +71,12 @@ __global__ void __launch_bounds__(512) chunk_step_kernel(const AxisStepArgs a) {
     const ChunkDev& T = a.ax.ck;
     const int n = a.ax.n;
     const int P = T.P;
+    const int np = P * RS;              // padded line length
     const int NL = a.lines_per_block;
     const int lgNL = __ffs(NL) - 1;
     const int l = threadIdx.x & (NL - 1);
     const int k = threadIdx.x >> lgNL;
-    const int nr = n + W;
+    const int nr = np + W;
     // staged tiles: x-lines [line][row] with an odd pitch (conflict-free per
     // lane), y/z-lines [row][32 lines] (a compile-time row stride)
     const int pitch = XL ? (nr | 1) : 32;
@@ -80,7 +84,8 @@ __global__ void __launch_bounds__(512) chunk_step_kernel(const AxisStepArgs a) {
     const int lst = XL ? pitch : 1;     // line stride
     const int cap = XL ? NL * pitch : nr * 32;
     float2* U2 = reinterpret_cast<float2*>(smem_raw);     // u (hi, lo); later the update's base / output
-    float* W0 = reinterpret_cast<float*>(U2 + cap);       // w0
+    float2* G2 = U2 + cap;                                // g = C u (hi, lo), own rows
+    float* W0 = reinterpret_cast<float*>(G2 + cap);       // w0
     float* TF = W0 + cap;                                 // [P][KP][NL] forward tails
     float* TB = TF + P * KP * NL;                         // [P][KP][NL] backward heads
     const long long ntot = a.ntot;
@@ -119,8 +124,9 @@ __global__ void __launch_bounds__(512) chunk_step_kernel(const AxisStepArgs a) {
             } else {
                 for (int i = tl; i < n; i += TPL) d[i] = make_float2(0.f, 0.f);
             }
+            // padded rows and the window overhang: zero
             for (int i = n + tl; i < pitch; i += TPL) d[i] = make_float2(0.f, 0.f);
-            for (int i = n + tl; i < pitch; i += TPL) W0[ll * pitch + i] = 0.f;
+            for (int i = np + tl; i < pitch; i += TPL) W0[ll * pitch + i] = 0.f;
         }
     } else {
         const long long g0 = l < nl ? line_base(l) : 0;
@@ -137,21 +143,19 @@ __global__ void __launch_bounds__(512) chunk_step_kernel(const AxisStepArgs a) {
                 *d = make_float2(0.f, 0.f);
             }
         }
-        for (int i = n + k; i < nr; i += P) {
-            U2[i * ust + l] = make_float2(0.f, 0.f);
-            W0[i * ust + l] = 0.f;
-        }
+        for (int i = n + k; i < nr; i += P) U2[i * ust + l] = make_float2(0.f, 0.f);
+        for (int i = np + k; i < nr; i += P) W0[i * ust + l] = 0.f;
     }
     cp_async_wait_all();
     __syncthreads();
 
     const int r0 = k * RS;
-    const int R = (k < P - 1) ? RS : n - r0;
     const float2* ul = U2 + l * lst;
     float* wl = W0 + l * lst;
     const int J = __ldg(T.J);
 
-    float gh[RS], gl[RS], y[RS];
+    float y[RS];
+    float2* gown = G2 + l * lst + r0 * ust;   // this thread's rows of g
 #pragma unroll
     for (int j = 0; j < RS; ++j) y[j] = 0.f;
 
@@ -206,20 +210,18 @@ __global__ void __launch_bounds__(512) chunk_step_kernel(const AxisStepArgs a) {
         tail_in(t);
 #pragma unroll
         for (int j = RS - 1; j >= 0; --j) {
-            if (j < R) {
-                const int i = r0 + j;
-                float gv[4], uv[4];
-                chunkstep::ld4<KP>(T.fg, i, gv);
-                chunkstep::ld4<KP>(T.fu, i, uv);
-                float z = y[j];
+            const int i = r0 + j;
+            float gv[4], uv[4];
+            chunkstep::ld4<KP>(T.fg, i, gv);
+            chunkstep::ld4<KP>(T.fu, i, uv);
+            float z = y[j];
 #pragma unroll
-                for (int c = 0; c < KP; ++c) z = fmaf(-gv[c], t[c], z);
+            for (int c = 0; c < KP; ++c) z = fmaf(-gv[c], t[c], z);
 #pragma unroll
-                for (int m = KP; m >= 1; --m)
-                    if (j + m < RS) z = fmaf(-uv[m - 1], y[j + m], z);
-                const float di = (KP <= 3) ? uv[3] : __ldg(T.fd + i);
-                y[j] = z * di;
-            }
+            for (int m = KP; m >= 1; --m)
+                if (j + m < RS) z = fmaf(-uv[m - 1], y[j + m], z);
+            const float di = (KP <= 3) ? uv[3] : __ldg(T.fd + i);
+            y[j] = z * di;
         }
         if (k > 0) {
 #pragma unroll
@@ -233,61 +235,56 @@ __global__ void __launch_bounds__(512) chunk_step_kernel(const AxisStepArgs a) {
         if (k == P - 1) return;
 #pragma unroll
         for (int j = 0; j < RS; ++j) {
-            if (j < R) {
-                float hv[4];
-                chunkstep::ld4<KP>(T.fh, r0 + j, hv);
-                float v = y[j];
+            float hv[4];
+            chunkstep::ld4<KP>(T.fh, r0 + j, hv);
+            float v = y[j];
 #pragma unroll
-                for (int c = 0; c < KP; ++c) v = fmaf(-hv[c], h[c], v);
-                y[j] = v;
-            }
+            for (int c = 0; c < KP; ++c) v = fmaf(-hv[c], h[c], v);
+            y[j] = v;
         }
     };
 
     // ---- P1: g = C u (double-float) fused with the forward sweep of w0 --------
 #pragma unroll
     for (int j = 0; j < RS; ++j) {
-        if (j < R) {
-            const int i = r0 + j;
-            float cv[NQ4 * 4];
+        const int i = r0 + j;
+        float cv[NQ4 * 4];
 #pragma unroll
-            for (int q = 0; q < NQ4; ++q) {
-                const float4 c4 = __ldg(T.cw + (size_t)i * NQ4 + q);
-                cv[4 * q] = c4.x;
-                cv[4 * q + 1] = c4.y;
-                cv[4 * q + 2] = c4.z;
-                cv[4 * q + 3] = c4.w;
-            }
-            const int fs = __float_as_int(cv[2 * W]);
-            if (!IGAPW_IDX("chunk P1 window", fs + W - 1, nr)) continue;
-            const float2* uu = ul + fs * ust;
-            float s, cc;
-            {
-                const float2 v = uu[0];
-                s = cv[0] * v.x;
-                cc = fmaf(cv[0], v.x, -s);
-                cc = fmaf(cv[0], v.y, cc);
-                cc = fmaf(cv[1], v.x, cc);
-            }
-#pragma unroll
-            for (int w = 1; w < W; ++w) {
-                const float2 v = uu[w * ust];
-                const float ch = cv[2 * w], cl = cv[2 * w + 1];
-                const float pr = ch * v.x;
-                float e = fmaf(ch, v.x, -pr);
-                e = fmaf(ch, v.y, e);
-                e = fmaf(cl, v.x, e);
-                float s2, er;
-                two_sum(s, pr, s2, er);
-                s = s2;
-                cc += er + e;
-            }
-            fast_two_sum(s, cc, gh[j], gl[j]);
-            fwd(j, i, gh[j]);
-        } else {
-            gh[j] = 0.f;
-            gl[j] = 0.f;
+        for (int q = 0; q < NQ4; ++q) {
+            const float4 c4 = __ldg(T.cw + (size_t)i * NQ4 + q);
+            cv[4 * q] = c4.x;
+            cv[4 * q + 1] = c4.y;
+            cv[4 * q + 2] = c4.z;
+            cv[4 * q + 3] = c4.w;
         }
+        const int fs = __float_as_int(cv[2 * W]);
+        if (!IGAPW_IDX("chunk P1 window", fs + W - 1, nr)) continue;
+        const float2* uu = ul + fs * ust;
+        float s, cc;
+        {
+            const float2 v = uu[0];
+            s = cv[0] * v.x;
+            cc = fmaf(cv[0], v.x, -s);
+            cc = fmaf(cv[0], v.y, cc);
+            cc = fmaf(cv[1], v.x, cc);
+        }
+#pragma unroll
+        for (int w = 1; w < W; ++w) {
+            const float2 v = uu[w * ust];
+            const float ch = cv[2 * w], cl = cv[2 * w + 1];
+            const float pr = ch * v.x;
+            float e = fmaf(ch, v.x, -pr);
+            e = fmaf(ch, v.y, e);
+            e = fmaf(cl, v.x, e);
+            float s2, er;
+            two_sum(s, pr, s2, er);
+            s = s2;
+            cc += er + e;
+        }
+        float gh, gl;
+        fast_two_sum(s, cc, gh, gl);
+        gown[j * ust] = make_float2(gh, gl);
+        fwd(j, i, gh);
     }
     if (k < P - 1) {
 #pragma unroll
@@ -299,8 +296,7 @@ __global__ void __launch_bounds__(512) chunk_step_kernel(const AxisStepArgs a) {
     finish_solve();
     // publish w0 for the residual windows of the neighbouring rows
 #pragma unroll
-    for (int j = 0; j < RS; ++j)
-        if (j < R) wl[(r0 + j) * ust] = y[j];
+    for (int j = 0; j < RS; ++j) wl[(r0 + j) * ust] = y[j];
     __syncthreads();
 
     // the base of the update: the accumulator of the earlier axes (y/z lines),
@@ -312,6 +308,7 @@ __global__ void __launch_bounds__(512) chunk_step_kernel(const AxisStepArgs a) {
             const float* ah = static_cast<const float*>(a.acc) + g0;
             const float* al = ah + ntot;
             const int rsi = (int)rs;
+            const int R = min(RS, n - r0);   // rows of the chunk inside the line
             for (int j = 0; j < R; ++j) {
                 if (!IGAPW_IDX("chunk base", g0 + (long long)j * rs, ntot)) continue;
                 float2* d = U2 + (r0 + j) * ust + l;
@@ -324,35 +321,34 @@ __global__ void __launch_bounds__(512) chunk_step_kernel(const AxisStepArgs a) {
     // ---- P3: rho = g - A w0 (double-float) fused with the forward sweep -------
 #pragma unroll
     for (int j = 0; j < RS; ++j) {
-        if (j < R) {
-            const int i = r0 + j;
-            float av[NQ4 * 4];
+        const int i = r0 + j;
+        float av[NQ4 * 4];
 #pragma unroll
-            for (int q = 0; q < NQ4; ++q) {
-                const float4 a4 = __ldg(T.aw + (size_t)i * NQ4 + q);
-                av[4 * q] = a4.x;
-                av[4 * q + 1] = a4.y;
-                av[4 * q + 2] = a4.z;
-                av[4 * q + 3] = a4.w;
-            }
-            const int fs = __float_as_int(av[2 * W]);
-            if (!IGAPW_IDX("chunk P3 window", fs + W - 1, nr)) continue;
-            const float* ww = wl + fs * ust;
-            float s = gh[j], cc = gl[j];
-#pragma unroll
-            for (int w = 0; w < W; ++w) {
-                const float x = ww[w * ust];
-                const float ah = -av[2 * w], al = -av[2 * w + 1];
-                const float pr = ah * x;
-                float e = fmaf(ah, x, -pr);
-                e = fmaf(al, x, e);
-                float s2, er;
-                two_sum(s, pr, s2, er);
-                s = s2;
-                cc += er + e;
-            }
-            fwd(j, i, s + cc);
+        for (int q = 0; q < NQ4; ++q) {
+            const float4 a4 = __ldg(T.aw + (size_t)i * NQ4 + q);
+            av[4 * q] = a4.x;
+            av[4 * q + 1] = a4.y;
+            av[4 * q + 2] = a4.z;
+            av[4 * q + 3] = a4.w;
         }
+        const int fs = __float_as_int(av[2 * W]);
+        if (!IGAPW_IDX("chunk P3 window", fs + W - 1, nr)) continue;
+        const float* ww = wl + fs * ust;
+        const float2 g = gown[j * ust];
+        float s = g.x, cc = g.y;
+#pragma unroll
+        for (int w = 0; w < W; ++w) {
+            const float x = ww[w * ust];
+            const float ah = -av[2 * w], al = -av[2 * w + 1];
+            const float pr = ah * x;
+            float e = fmaf(ah, x, -pr);
+            e = fmaf(al, x, e);
+            float s2, er;
+            two_sum(s, pr, s2, er);
+            s = s2;
+            cc += er + e;
+        }
+        fwd(j, i, s + cc);
     }
     if (k < P - 1) {
 #pragma unroll
@@ -370,32 +366,32 @@ __global__ void __launch_bounds__(512) chunk_step_kernel(const AxisStepArgs a) {
     unsigned bad = 0;
     float* oh = static_cast<float*>((MODE == 0 || MODE == 1) ? a.acc : a.u_out);
     const long long gl0 = (!XL && l < nl) ? line_base(l) : 0;
-    float* ohl = oh + gl0;           // this line's first element (y/z lines)
-    float* oll = ohl + ntot;
-    const int rsi = (int)rs;
+    // this thread's first row of the line (y/z lines), advanced row by row
+    float* oq = oh + gl0 + (long long)r0 * rs;
+    const long long rsl = rs;
 #pragma unroll
     for (int j = 0; j < RS; ++j) {
-        if (j < R) {
-            const int i = r0 + j;
-            const float w0 = wl[i * ust];
-            const float ph = dth * w0;
-            float pe = fmaf(dth, w0, -ph);
-            pe = fmaf(dtl, w0, pe);
-            pe = fmaf(dth, y[j], pe);
-            float2* bp = U2 + l * lst + i * ust;
-            const float2 b = *bp;
-            float s, e;
-            two_sum(b.x, ph, s, e);
-            float hi, lo;
-            fast_two_sum(s, b.y + (pe + e), hi, lo);
-            if (!isfinite(hi)) bad = 1;
-            if (XL) {
-                *bp = make_float2(hi, lo);
-            } else if (l < nl) {
-                if (!IGAPW_IDX("chunk out", gl0 + (long long)i * rs, ntot)) continue;
-                ohl[i * rsi] = hi;
-                oll[i * rsi] = lo;
+        const int i = r0 + j;
+        const float w0 = wl[i * ust];
+        const float ph = dth * w0;
+        float pe = fmaf(dth, w0, -ph);
+        pe = fmaf(dtl, w0, pe);
+        pe = fmaf(dth, y[j], pe);
+        float2* bp = U2 + l * lst + i * ust;
+        const float2 b = *bp;
+        float s, e;
+        two_sum(b.x, ph, s, e);
+        float hi, lo;
+        fast_two_sum(s, b.y + (pe + e), hi, lo);
+        if (!isfinite(hi)) bad = 1;
+        if (XL) {
+            *bp = make_float2(hi, lo);
+        } else {
+            if (l < nl && i < n && IGAPW_IDX("chunk out", gl0 + (long long)i * rs, ntot)) {
+                oq[0] = hi;
+                oq[ntot] = lo;
             }
+            oq += rsl;
         }
     }
     if constexpr (XL) {
@@ -423,10 +419,11 @@ static cudaError_t run_chunk_step(const AxisStepArgs& a, cudaStream_t st) {
     if (P <= 0 || a.ax.ck.rows != RS || (NL != 8 && NL != 16 && NL != 32) || NL * P > 512 ||
         (long long)(P - 1) * RS >= n || (long long)P * RS < n)
         return cudaErrorInvalidValue;
+    const int np = P * RS;
     if ((a.axis == 0) != XL) return cudaErrorInvalidValue;
     const long long nlines = XL ? (long long)a.n[1] * a.n[2]
                                 : (a.axis == 1 ? (long long)a.n[0] * a.n[2] : (long long)a.n[0] * a.n[1]);
-    const size_t sm = chunkstep::smem_bytes(XL, n, W, NL, P, KP);
+    const size_t sm = chunkstep::smem_bytes(XL, np, W, NL, P, KP);
     int dev = 0, lim = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&lim, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);

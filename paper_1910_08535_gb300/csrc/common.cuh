@@ -120,20 +120,21 @@ struct LineSys {
 
 // Packed FP32 tables of the chunked explicit step (chunkstep.cuh), built once
 // per axis by launch_chunk_tables from the FP64 factors.  A line of n rows is
-// cut into P chunks of `rows` rows (the last one holds the rest); chunk k's
+// padded to P * rows rows (decoupled identity rows) and cut into P chunks of
+// `rows` rows; chunk k's
 // partitioned solve takes the true tail of chunk k-1 as the local tail plus
 // the composed spike operators of up to J-1 earlier chunks (J = P unless the
 // operators decay below 1e-16 sooner).
 struct ChunkDev {
     int rows;             // rows per chunk (the kernel's compile-time chunk length)
     int P;                // chunks per line
-    const float4* cw;     // [n][nq4]: C window as (hi, lo) pairs, then fstart (int bits)
-    const float4* aw;     // [n][nq4]: A window, same layout
-    const float4* fl;     // [n]: l_{i,i-1} .. l_{i,i-p}
-    const float4* fu;     // [n]: u_{i,i+1} .. u_{i,i+p}; dinv in .w when p <= 3
-    const float* fd;      // [n]: 1 / u_{i,i}
-    const float4* fg;     // [n]: forward spike of row i (columns: the previous chunk's last p rows)
-    const float4* fh;     // [n]: backward spike (columns: the next chunk's first p rows)
+    const float4* cw;     // [np][nq4]: C window as (hi, lo) pairs, then fstart (int bits)
+    const float4* aw;     // [np][nq4]: A window, same layout
+    const float4* fl;     // [np]: l_{i,i-1} .. l_{i,i-p}
+    const float4* fu;     // [np]: u_{i,i+1} .. u_{i,i+p}; dinv in .w when p <= 3
+    const float* fd;      // [np]: 1 / u_{i,i}
+    const float4* fg;     // [np]: forward spike of row i (columns: the previous chunk's last p rows)
+    const float4* fh;     // [np]: backward spike (columns: the next chunk's first p rows)
     const float* psf;     // [P][P][p][p]: psf[k][d] = Phi_{k-1} ... Phi_{k-d} (forward tails)
     const float* psb;     // [P][P][p][p]: psb[k][d] = Theta_{k+1} ... Theta_{k+d} (backward heads)
     const int* J;         // chunks that enter a composed tail or head (device scalar)

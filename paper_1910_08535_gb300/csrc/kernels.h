@@ -42,13 +42,14 @@ struct FactorArgs {
 
 // Packed tables of the chunked step (chunkstep.cuh) from the FP64 factors.
 struct ChunkTableArgs {
-    int n, p, W, RS, P;
+    int n, p, W, RS, P;           // lines padded to P * RS rows
     const double *L, *U, *dinv;   // factor_kernel output, [n][p] / [n]
     const float2 *Adf, *Cdf;      // [n][W] double-float windows
     const int* fstart;
-    double* work;                 // [2 n p]
-    float4 *cw, *aw, *fl, *fu, *fg, *fh;
-    float *fd, *psf, *psb;
+    double* work;                 // [2 P RS p]
+    float4 *cw, *aw;              // [P RS][nq4]
+    float4 *fl, *fu, *fg, *fh;    // [P RS]
+    float *fd, *psf, *psb;        // [P RS], [P][P][p][p]
     int* J;
 };
 void launch_chunk_tables(const ChunkTableArgs& a, cudaStream_t st);
@@ -103,6 +104,23 @@ struct SourceArgs {
     long long ntot;
 };
 cudaError_t launch_source(const SourceArgs& a, int fp64, cudaStream_t st);
+
+// b = amp (x)_a v_a, v_a = TW_a sin(k_a pi x_a) at the axis' points (separable
+// sine source); v: three device buffers of n_a doubles (the context sets
+// v[d] = 1.0 once for the absent axes).
+struct SineSourceArgs {
+    int dim;
+    int n[3];
+    int q[3];
+    AxisDev ax[3];
+    const double* qx[3];
+    double k[3];
+    double amp;
+    double* v[3];
+    void* out;
+    long long ntot;
+};
+cudaError_t launch_source_sine(const SineSourceArgs& a, int fp64, cudaStream_t st);
 
 // b += face term of a Neumann axis: sum over the other axes' point windows of
 // their test weights times g, added to the rows at the axis end.

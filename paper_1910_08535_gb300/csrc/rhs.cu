@@ -346,6 +346,64 @@ __global__ void __launch_bounds__(256) source_pw_xrow_kernel(const SourceArgs a)
     }
 }
 
+// ---------------------------------------------------------------------------
+// Source RHS of a separable source f = amp prod_a sin(k_a pi x_a): because the
+// tests are tensor products, b = amp (x)_a v_a with the 1D factors
+// v_a[i] = sum_w TW_a[i][w] sin(k_a pi x_{pstart[i] + w}) (the same sums the
+// axis passes of the general source RHS form), in FP64.
+// ---------------------------------------------------------------------------
+__global__ void sine_factor_kernel(int n, int wq, int Q, const int* __restrict__ pstart,
+                                   const double* __restrict__ tw, const double* __restrict__ qx, double k,
+                                   double* __restrict__ v) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double s = 0.0;
+    for (int w = 0; w < wq; ++w) {
+        const int q = pstart[i] + w;
+        const double t = tw[(size_t)i * wq + w];
+        if (q >= Q || t == 0.0) continue;
+        s = fma(t, sinpi(k * qx[q]), s);
+    }
+    v[i] = s;
+}
+
+template <bool PAIR>
+__global__ void __launch_bounds__(256) sine_outer_kernel(long long ntot, int nx, int ny, double amp,
+                                                         const double* __restrict__ vx, const double* __restrict__ vy,
+                                                         const double* __restrict__ vz, void* out) {
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= ntot) return;
+    const long long nxy = (long long)nx * ny;
+    const int z = (int)(e / nxy);
+    const long long r = e - (long long)z * nxy;
+    const int y = (int)(r / nx), x = (int)(r - (long long)y * nx);
+    const double b = amp * vz[z] * vy[y] * vx[x];
+    if constexpr (PAIR) {
+        float h, l;
+        split_double(b, h, l);
+        static_cast<float*>(out)[e] = h;
+        static_cast<float*>(out)[e + ntot] = l;
+    } else {
+        static_cast<double*>(out)[e] = b;
+    }
+}
+
+cudaError_t launch_source_sine(const SineSourceArgs& a, int fp64, cudaStream_t st) {
+    for (int d = 0; d < a.dim; ++d) {
+        const AxisDev& X = a.ax[d];
+        sine_factor_kernel<<<(X.n + 127) / 128, 128, 0, st>>>(X.n, X.wq, a.q[d], X.pstart, X.TW.d, a.qx[d], a.k[d],
+                                                              a.v[d]);
+    }
+    const long long blocks = (a.ntot + 255) / 256;
+    if (fp64)
+        sine_outer_kernel<false><<<(unsigned)blocks, 256, 0, st>>>(a.ntot, a.n[0], a.n[1], a.amp, a.v[0], a.v[1],
+                                                                  a.v[2], a.out);
+    else
+        sine_outer_kernel<true><<<(unsigned)blocks, 256, 0, st>>>(a.ntot, a.n[0], a.n[1], a.amp, a.v[0], a.v[1],
+                                                                 a.v[2], a.out);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_neumann(const NeumannArgs& a, int fp64, cudaStream_t st) {
     long long face = 1;
     for (int k = 0; k < a.dim; ++k)

@@ -50,6 +50,7 @@ _SIGS = {
     'igapw_basis_table': (_I, [_VP, _I, ctypes.POINTER(_D), ctypes.POINTER(_I)]),
     'igapw_rhs_source': (_I, [_VP, _VP, _VP]),
     'igapw_rhs_source_noalloc': (_I, [_VP, _VP, _VP]),
+    'igapw_rhs_source_sine': (_I, [_VP, _D, ctypes.POINTER(_D), _VP]),
     'igapw_rhs_neumann': (_I, [_VP, _I, _I, _VP, _VP]),
     'igapw_apply': (_I, [_VP, _I, _D, _VP, _VP]),
     'igapw_assemble_1d': (_I, [_VP, _I, _I, ctypes.POINTER(_D)]),
@@ -180,6 +181,11 @@ def igapw_rhs_source_noalloc(ctx, f, b):
     static device array instead of memory allocated on first use (for callers
     that cannot let the library allocate; see include/igapw.h)."""
     _check(load().igapw_rhs_source_noalloc(ctx, _dptr(f), _dptr(b)), ctx)
+
+
+def igapw_rhs_source_sine(ctx, amp, k, b):
+    arr = (_D * len(k))(*[float(x) for x in k])
+    _check(load().igapw_rhs_source_sine(ctx, float(amp), arr, _dptr(b)), ctx)
 
 
 def igapw_rhs_neumann(ctx, axis, side, g, b):
@@ -417,6 +423,14 @@ class Context:
     def rhs_source(self, f, out=None):
         out = self.empty() if out is None else self._coefs(out, 'rhs_source: out')
         igapw_rhs_source(self.ctx, self._samples(f, 'rhs_source: f', range(self.dim)), out)
+        return out
+
+    def rhs_source_sine(self, amp, k, out=None):
+        """igapw_rhs_source_sine: b = T(amp prod_a sin(k_a pi x_a)), source evaluated on the device."""
+        out = self.empty() if out is None else self._coefs(out, 'rhs_source_sine: out')
+        if len(k) != self.dim:
+            raise IgapwError(IGAPW_ERR_ARG, f'rhs_source_sine: {len(k)} wave numbers for dim {self.dim}')
+        igapw_rhs_source_sine(self.ctx, amp, k, out)
         return out
 
     def rhs_neumann(self, axis, side, g, b):

@@ -12,14 +12,14 @@ stream and overlaps on the GPU with every other admitted request:
 
   heat     host-to-device copy of the initial coefficients, `steps` explicit
            steps (one CUDA graph), device-to-host copy of the result;
-  poisson  the manufactured source prod_a sin(k_a pi x_a) sampled at the
-           quadrature points on the device, the source RHS, the multi-D
+  poisson  the source RHS of the manufactured source prod_a sin(k_a pi x_a)
+           (evaluated by the library at the quadrature points), the multi-D
            Poisson solve, device-to-host copy of the solution.
 
 Completion is detected by polling a CUDA event per slot; a request's latency
-is completion time minus arrival time.  Every arithmetic step of the method
-runs in libigapw; this module schedules, and samples the source (input
-generation) with elementwise torch operations.
+is completion time minus arrival time.  Every arithmetic step of a request
+runs in libigapw (no torch kernel on the request path); this module
+schedules and copies.
 """
 import collections
 import dataclasses
@@ -114,11 +114,11 @@ def slot_bytes(shape):
 
 
 def transient_bytes(shape):
-    """Device bytes a request holds only while it runs: the source samples of
-    a Poisson request (upper bound on the quadrature grid)."""
-    if shape.kind != 'poisson':
-        return 0
-    return (8 if shape.precision == 'fp64' else 4) * shape.nquad
+    """Device bytes a request holds only while it runs, beyond its slot: none
+    (a Poisson request's source is evaluated by the library into the slot's
+    right-hand-side tensor; a heat request steps the slot's state).  The
+    scheduler keeps the accounting for request kinds that would need some."""
+    return 0
 
 
 class Slot:
@@ -140,9 +140,7 @@ class Slot:
             self.u = self.ctx.empty()
             if shape.kind == 'poisson':
                 self.b = self.ctx.empty()
-                self.qx = [torch.from_numpy(self.ctx.quad_points(a)[0]).to('cuda', hdtype) for a in range(shape.dim)]
         self.hdtype = hdtype
-        self.f = None           # source samples: allocated per request, dropped at completion
         self.host_out = torch.empty(planes * self.ctx.ntot, dtype=hdtype).pin_memory()
         if shape.kind == 'heat':
             u0 = base_state(shape).ravel()
@@ -166,24 +164,15 @@ class Slot:
                 self.u.view(-1).copy_(self.host_in, non_blocking=True)
                 self.ctx.step(self.u, req.dt_h2 / (sh.n_elem ** 2 * sh.dim), req.steps)
             else:
-                self.f = torch.empty(tuple(len(q) for q in reversed(self.qx)), dtype=self.hdtype, device='cuda')
-                scale = float(np.pi ** 2 * sum(k * k for k in req.k))
-                fac = [torch.sin((req.k[a] * np.pi) * self.qx[a]) for a in range(sh.dim)]
-                if sh.dim == 2:
-                    torch.mul(fac[1].view(-1, 1), fac[0].view(1, -1) * scale, out=self.f)
-                else:
-                    torch.mul(fac[2].view(-1, 1, 1), (fac[1].view(-1, 1) * fac[0].view(1, -1) * scale).unsqueeze(0),
-                              out=self.f)
-                self.ctx.rhs_source(self.f, out=self.b)
+                amp = float(np.pi ** 2 * sum(k * k for k in req.k))
+                self.ctx.rhs_source_sine(amp, req.k, out=self.b)
                 self.ctx.solve(self.b, out=self.u)
             self.host_out.copy_(self.u.view(-1), non_blocking=True)
             self.done.record(self.stream)
         self.req = req
 
     def retire(self):
-        """After completion: drop the request's transient buffers (their
-        memory goes back to the stream's allocator cache)."""
-        self.f = None
+        """After completion: the slot is free for the next request."""
         self.req = None
 
     def result(self):

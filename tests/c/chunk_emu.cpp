@@ -66,13 +66,14 @@ static ChunkDev build_tables(const AxisIn& ax, int p, int W) {
     int* fs = exact<int>(n);
     for (int i = 0; i < n; ++i) fs[i] = ax.fs[i];
     const int RS = 17, P = (n + RS - 1) / RS, q4 = (2 * W + 4) / 4;
+    const size_t np = (size_t)P * RS;   // padded line
     ChunkTableArgs ca{};
     ca.n = n; ca.p = p; ca.W = W; ca.RS = RS; ca.P = P;
     ca.L = L; ca.U = U; ca.dinv = dinv; ca.Adf = Adf; ca.Cdf = Cdf; ca.fstart = fs;
-    ca.work = exact<double>((size_t)2 * n * p);
-    ca.cw = exact<float4>((size_t)n * q4); ca.aw = exact<float4>((size_t)n * q4);
-    ca.fl = exact<float4>(n); ca.fu = exact<float4>(n); ca.fg = exact<float4>(n); ca.fh = exact<float4>(n);
-    ca.fd = exact<float>(n);
+    ca.work = exact<double>(2 * np * p);
+    ca.cw = exact<float4>(np * q4); ca.aw = exact<float4>(np * q4);
+    ca.fl = exact<float4>(np); ca.fu = exact<float4>(np); ca.fg = exact<float4>(np); ca.fh = exact<float4>(np);
+    ca.fd = exact<float>(np);
     ca.psf = exact<float>((size_t)P * P * p * p); ca.psb = exact<float>((size_t)P * P * p * p);
     ca.J = exact<int>(1);
     emu_threadIdx = {}; emu_blockIdx = {}; emu_blockDim = {1, 1, 1};
@@ -90,7 +91,7 @@ static void run(const AxisStepArgs& a) {
     const int n = a.ax.n, P = a.ax.ck.P, NL = a.lines_per_block;
     const long long nlines = XL ? (long long)a.n[1] * a.n[2]
                                 : (a.axis == 1 ? (long long)a.n[0] * a.n[2] : (long long)a.n[0] * a.n[1]);
-    const size_t sm = chunkstep::smem_bytes(XL, n, W, NL, P, KP);
+    const size_t sm = chunkstep::smem_bytes(XL, P * 17, W, NL, P, KP);
     const long long blocks = (nlines + NL - 1) / NL;
     const int threads = NL * P;
     for (long long b = 0; b < blocks; ++b) {
