@@ -433,21 +433,29 @@ def measure_ladder(stream, flush, hbm_peak, reps=5):
         for ne, p in sizes:
             row = {'dim': dim, 'n_elem': ne, 'degree': p}
             for test in ('pw', 'galerkin'):
-                with torch.cuda.stream(stream):
-                    c = Context(dim=dim, n_elem=ne, degree=p, nq=p + 1, test=test, precision='fp32r', stream=stream)
-                    u = c.from_numpy(workloads.normal_coeffs(c.shape, seed=ne))
-                    dt = 0.05 / ne ** 2
-                    t = _time_events(stream, lambda: c.step(u, dt, 1), reps, flush)
-                    c.sync()
-                    shapes = [c.get_step_shape(a) for a in range(dim)]
-                row['dof'] = c.ntot
-                row[test] = {'step_us': t * 1e6, 'dof_updates_per_s': c.ntot / t,
-                             'alg_hbm_frac': 16 * c.ntot / t / 1e9 / hbm_peak,
-                             'kernels': '/'.join(f'{k}{nl}' for k, nl in shapes)}
-                c.close()
-                del u
-                torch.cuda.empty_cache()
-            row['pw_over_galerkin'] = row['pw']['dof_updates_per_s'] / row['galerkin']['dof_updates_per_s']
+                c = None
+                try:
+                    with torch.cuda.stream(stream):
+                        c = Context(dim=dim, n_elem=ne, degree=p, nq=p + 1, test=test, precision='fp32r',
+                                    stream=stream)
+                        u = c.from_numpy(workloads.normal_coeffs(c.shape, seed=ne))
+                        dt = 0.05 / ne ** 2
+                        t = _time_events(stream, lambda: c.step(u, dt, 1), reps, flush)
+                        c.sync()
+                        shapes = [c.get_step_shape(a) for a in range(dim)]
+                    row['dof'] = c.ntot
+                    row[test] = {'step_us': t * 1e6, 'dof_updates_per_s': c.ntot / t,
+                                 'alg_hbm_frac': 16 * c.ntot / t / 1e9 / hbm_peak,
+                                 'kernels': '/'.join(f'{k}{nl}' for k, nl in shapes)}
+                except Exception as ex:      # a grid no step kernel takes (lines too long)
+                    row[test] = {'error': str(ex)[:160]}
+                finally:
+                    if c is not None:
+                        c.close()
+                    u = None
+                    torch.cuda.empty_cache()
+            if 'dof_updates_per_s' in row['pw'] and 'dof_updates_per_s' in row['galerkin']:
+                row['pw_over_galerkin'] = row['pw']['dof_updates_per_s'] / row['galerkin']['dof_updates_per_s']
             out.append(row)
     return out
 

@@ -49,10 +49,26 @@ __host__ __device__ inline size_t smem_bytes(bool xl, int np, int W, int NL, int
     return cap * 8 + cap * 8 + cap * 4 + (size_t)2 * P * KP * NL * 4;
 }
 
+// Read-only table loads that ask L1 to keep the line (evict_last): the
+// tables (a few tens of KB, read by every block) would otherwise be evicted
+// by the streaming state tiles that pass through L1 on their way to shared
+// memory, and every row's table reads would go to L2.
+__device__ __forceinline__ float4 ld_keep(const float4* p) {
+#ifdef IGAPW_HOST_EMU
+    return *p;
+#else
+    float4 v;
+    asm("ld.global.nc.L1::evict_last.v4.f32 {%0, %1, %2, %3}, [%4];"
+        : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+        : "l"(p));
+    return v;
+#endif
+}
+
 // Loads v[0..KP) of a float4 table row.
 template <int KP>
 __device__ __forceinline__ void ld4(const float4* t, int i, float (&v)[4]) {
-    const float4 q = __ldg(t + i);
+    const float4 q = ld_keep(t + i);
     v[0] = q.x;
     v[1] = q.y;
     v[2] = q.z;
@@ -251,7 +267,7 @@ __global__ void __launch_bounds__(512) chunk_step_kernel(const AxisStepArgs a) {
         float cv[NQ4 * 4];
 #pragma unroll
         for (int q = 0; q < NQ4; ++q) {
-            const float4 c4 = __ldg(T.cw + (size_t)i * NQ4 + q);
+            const float4 c4 = chunkstep::ld_keep(T.cw + (size_t)i * NQ4 + q);
             cv[4 * q] = c4.x;
             cv[4 * q + 1] = c4.y;
             cv[4 * q + 2] = c4.z;
@@ -325,7 +341,7 @@ __global__ void __launch_bounds__(512) chunk_step_kernel(const AxisStepArgs a) {
         float av[NQ4 * 4];
 #pragma unroll
         for (int q = 0; q < NQ4; ++q) {
-            const float4 a4 = __ldg(T.aw + (size_t)i * NQ4 + q);
+            const float4 a4 = chunkstep::ld_keep(T.aw + (size_t)i * NQ4 + q);
             av[4 * q] = a4.x;
             av[4 * q + 1] = a4.y;
             av[4 * q + 2] = a4.z;
