@@ -80,7 +80,7 @@ namespace {
 constexpr int kPoissonRefineF64 = 3;
 // chunked explicit step: rows per chunk (the kernels' compile-time length) and
 // the most chunks a line may have (512 threads at 16 lines per block)
-constexpr int kChunkRows = 17;
+constexpr int kChunkRows = IGAPW_CHUNK_ROWS;
 constexpr int kChunkMaxP = 32;
 
 int fail(igapw_ctx* c, int code, const std::string& msg) {

@@ -230,14 +230,15 @@ __global__ void __launch_bounds__(512) chunk_step_kernel(const AxisStepArgs a) {
             float gv[4], uv[4];
             chunkstep::ld4<KP>(T.fg, i, gv);
             chunkstep::ld4<KP>(T.fu, i, uv);
-            float z = y[j];
+            const float di = (KP <= 3) ? uv[3] : __ldg(T.fd + i);
+            // rows scaled by 1 / u_ii: only the last FMA waits on y[j+1]
+            float z = y[j] * di;
 #pragma unroll
             for (int c = 0; c < KP; ++c) z = fmaf(-gv[c], t[c], z);
 #pragma unroll
             for (int m = KP; m >= 1; --m)
                 if (j + m < RS) z = fmaf(-uv[m - 1], y[j + m], z);
-            const float di = (KP <= 3) ? uv[3] : __ldg(T.fd + i);
-            y[j] = z * di;
+            y[j] = z;
         }
         if (k > 0) {
 #pragma unroll

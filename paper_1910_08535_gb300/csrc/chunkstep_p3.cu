@@ -7,10 +7,10 @@ namespace {
 template <int W>
 cudaError_t pick_mode(const AxisStepArgs& a, int mode, cudaStream_t st) {
     switch (mode) {
-        case 0: return run_chunk_step<3, W, 0, 17>(a, st);
-        case 1: return run_chunk_step<3, W, 1, 17>(a, st);
-        case 2: return run_chunk_step<3, W, 2, 17>(a, st);
-        case 3: return run_chunk_step<3, W, 3, 17>(a, st);
+        case 0: return run_chunk_step<3, W, 0, IGAPW_CHUNK_ROWS>(a, st);
+        case 1: return run_chunk_step<3, W, 1, IGAPW_CHUNK_ROWS>(a, st);
+        case 2: return run_chunk_step<3, W, 2, IGAPW_CHUNK_ROWS>(a, st);
+        case 3: return run_chunk_step<3, W, 3, IGAPW_CHUNK_ROWS>(a, st);
     }
     return cudaErrorInvalidValue;
 }

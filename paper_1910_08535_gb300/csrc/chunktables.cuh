@@ -88,10 +88,13 @@ __global__ void chunk_tables_kernel(ChunkTableArgs a) {
         aw[2 * W] = __int_as_float(fs);
         float fl[4] = {0.f, 0.f, 0.f, 0.f}, fu[4] = {0.f, 0.f, 0.f, 0.f};
         float fg[4] = {0.f, 0.f, 0.f, 0.f}, fh[4] = {0.f, 0.f, 0.f, 0.f};
+        // the backward rows are stored scaled by 1 / u_ii, so that the
+        // recurrence x_i = dinv_i yhat_i - sum (G dinv)_i t - sum (u dinv)_{i,m} x_{i+m}
+        // has one FMA per row on its dependency chain
         for (int m = 0; m < p; ++m) {
             fl[m] = (float)Lf(i, m + 1);
-            fu[m] = (float)Uf(i, m + 1);
-            fg[m] = (float)G[i * p + m];
+            fu[m] = (float)(Uf(i, m + 1) * Df(i));
+            fg[m] = (float)(G[i * p + m] * Df(i));
             fh[m] = (float)H[i * p + m];
         }
         if (p <= 3) fu[3] = (float)Df(i);

@@ -131,9 +131,9 @@ struct ChunkDev {
     const float4* cw;     // [np][nq4]: C window as (hi, lo) pairs, then fstart (int bits)
     const float4* aw;     // [np][nq4]: A window, same layout
     const float4* fl;     // [np]: l_{i,i-1} .. l_{i,i-p}
-    const float4* fu;     // [np]: u_{i,i+1} .. u_{i,i+p}; dinv in .w when p <= 3
+    const float4* fu;     // [np]: u_{i,i+1} .. u_{i,i+p} times 1/u_ii; 1/u_ii in .w when p <= 3
     const float* fd;      // [np]: 1 / u_{i,i}
-    const float4* fg;     // [np]: forward spike of row i (columns: the previous chunk's last p rows)
+    const float4* fg;     // [np]: forward spike of row i times 1/u_ii (columns: the previous chunk's last p rows)
     const float4* fh;     // [np]: backward spike (columns: the next chunk's first p rows)
     const float* psf;     // [P][P][p][p]: psf[k][d] = Phi_{k-1} ... Phi_{k-d} (forward tails)
     const float* psb;     // [P][P][p][p]: psb[k][d] = Theta_{k+1} ... Theta_{k+d} (backward heads)

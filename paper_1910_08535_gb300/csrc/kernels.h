@@ -9,6 +9,10 @@ struct igapw_ctx;
 #include "common.cuh"
 
 #define IGAPW_MAXP 4
+// rows per chunk of the chunked explicit step (the kernels' compile-time chunk length)
+#ifndef IGAPW_CHUNK_ROWS
+#define IGAPW_CHUNK_ROWS 17
+#endif
 
 namespace igapw {
 

@@ -65,7 +65,7 @@ static ChunkDev build_tables(const AxisIn& ax, int p, int W) {
     }
     int* fs = exact<int>(n);
     for (int i = 0; i < n; ++i) fs[i] = ax.fs[i];
-    const int RS = 17, P = (n + RS - 1) / RS, q4 = (2 * W + 4) / 4;
+    const int RS = IGAPW_CHUNK_ROWS, P = (n + RS - 1) / RS, q4 = (2 * W + 4) / 4;
     const size_t np = (size_t)P * RS;   // padded line
     ChunkTableArgs ca{};
     ca.n = n; ca.p = p; ca.W = W; ca.RS = RS; ca.P = P;
@@ -91,7 +91,7 @@ static void run(const AxisStepArgs& a) {
     const int n = a.ax.n, P = a.ax.ck.P, NL = a.lines_per_block;
     const long long nlines = XL ? (long long)a.n[1] * a.n[2]
                                 : (a.axis == 1 ? (long long)a.n[0] * a.n[2] : (long long)a.n[0] * a.n[1]);
-    const size_t sm = chunkstep::smem_bytes(XL, P * 17, W, NL, P, KP);
+    const size_t sm = chunkstep::smem_bytes(XL, P * IGAPW_CHUNK_ROWS, W, NL, P, KP);
     const long long blocks = (nlines + NL - 1) / NL;
     const int threads = NL * P;
     for (long long b = 0; b < blocks; ++b) {
@@ -106,7 +106,7 @@ static void run(const AxisStepArgs& a) {
                 emu_blockDim = {(unsigned)threads, 1, 1};
                 emu_barrier = &bar;
                 emu_smem_ptr = smem;
-                chunk_step_kernel<KP, W, MODE, 17>(a);
+                chunk_step_kernel<KP, W, MODE, IGAPW_CHUNK_ROWS>(a);
             });
         for (auto& t : ts) t.join();
         std::free(smem);
