@@ -372,6 +372,10 @@ int enqueue_steps(igapw_ctx* c, double dt, int nsteps, void* u, cudaStream_t st)
                 a.status = c->status;
                 a.cfg = c->step_cfg[ax];
                 a.lines_per_block = c->step_nl[ax];
+                // chunked launches overlap their predecessor (programmatic dependent
+                // launch): each waits on the device before it reads what the
+                // previous launch writes (chunkstep.cuh)
+                a.pdl = a.cfg == 3 ? 1 : 0;
                 const int mode = c->dim == 1 ? 3 : (ax == 0 ? 0 : (ax == c->dim - 1 ? 2 : 1));
                 cudaError_t e = launch_axis_step(a, mode, fp64(c), c->p, st);
                 if (e != cudaSuccess) return fail(c, IGAPW_ERR_CUDA, std::string("axis step: ") + cudaGetErrorString(e));

@@ -65,6 +65,23 @@ __device__ __forceinline__ float4 ld_keep(const float4* p) {
 #endif
 }
 
+// Programmatic dependent launch (the three per-axis launches of a step run
+// back to back on one stream): wait() blocks until the previous kernel of the
+// stream has completed and its writes are visible; launch_dependents() lets
+// the next kernel's blocks start once every block of this one has started.
+// Both are no-ops for a launch without the programmatic-serialization
+// attribute.
+__device__ __forceinline__ void griddep_wait() {
+#ifndef IGAPW_HOST_EMU
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+#endif
+}
+__device__ __forceinline__ void griddep_launch_dependents() {
+#ifndef IGAPW_HOST_EMU
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+#endif
+}
+
 // Loads v[0..KP) of a float4 table row.
 template <int KP>
 __device__ __forceinline__ void ld4(const float4* t, int i, float (&v)[4]) {
@@ -121,6 +138,18 @@ __global__ void __launch_bounds__(512) chunk_step_kernel(const AxisStepArgs a) {
         return L;
     };
     const float* uh = static_cast<const float*>(a.u);
+
+    // Dependencies within a step (x, y, z launches): the x launch reads u as
+    // the previous step's z launch left it, so it waits for that launch before
+    // anything and only then lets the y launch start; the y and z launches
+    // read u (final for the step) right away and wait for their predecessor
+    // only before they read its accumulator (z also before it writes u).
+    if constexpr (XL) {
+        chunkstep::griddep_wait();
+        chunkstep::griddep_launch_dependents();
+    } else {
+        chunkstep::griddep_launch_dependents();
+    }
 
     // ---- stage u (all rows of the block's lines) and zero the pad rows --------
     // x-lines are copied line by line, TPL consecutive threads per line
@@ -319,6 +348,7 @@ __global__ void __launch_bounds__(512) chunk_step_kernel(const AxisStepArgs a) {
     // the base of the update: the accumulator of the earlier axes (y/z lines),
     // staged into the dead u tile while the residual and the correction run
     if constexpr (!XL) {
+        chunkstep::griddep_wait();   // the previous axis' accumulator is complete
         if (l < nl) {
             // 32-bit row offsets from per-line pointers (a line spans < 2^31 elements)
             const long long g0 = line_base(l) + (long long)r0 * rs;
@@ -451,7 +481,18 @@ static cudaError_t run_chunk_step(const AxisStepArgs& a, cudaStream_t st) {
         if (e != cudaSuccess) return e;
     }
     const long long blocks = (nlines + NL - 1) / NL;
-    kern<<<(unsigned)blocks, NL * P, sm, st>>>(a);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)blocks);
+    cfg.blockDim = dim3((unsigned)(NL * P));
+    cfg.dynamicSmemBytes = sm;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = a.pdl ? 1 : 0;
+    cudaError_t e = cudaLaunchKernelEx(&cfg, kern, a);
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 

@@ -168,6 +168,8 @@ struct AxisStepArgs {
     int cfg;                // -1: the launcher's own choice; else forced with lines_per_block:
                             // 0 staged tables, 1 tables in global memory, 2 staged 16 columns,
                             // 3 the chunked register kernel (FP32 pairs; 32, 16 or 8 lines)
+    int pdl;                // chunked kernel: launch with programmatic stream serialization
+                            // (the step's launches overlap; see chunkstep.cuh)
     long long ntot;
     AxisDev ax;
     const void* u;
