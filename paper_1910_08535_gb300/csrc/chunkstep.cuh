@@ -65,17 +65,6 @@ __device__ __forceinline__ float4 ld_keep(const float4* p) {
 #endif
 }
 
-// State loads that bypass L1 (ld.global.cg: cached in L2 only): the state
-// tiles stream through once, and L1 stays free for the tables that every row
-// reads.
-__device__ __forceinline__ float ld_stream(const float* p) {
-#ifdef IGAPW_HOST_EMU
-    return *p;
-#else
-    return __ldcg(p);
-#endif
-}
-
 // Programmatic dependent launch (the three per-axis launches of a step run
 // back to back on one stream): wait() blocks until the previous kernel of the
 // stream has completed and its writes are visible; launch_dependents() lets
@@ -172,10 +161,10 @@ __global__ void __launch_bounds__(512) chunk_step_kernel(const AxisStepArgs a) {
             float2* d = U2 + ll * pitch;
             if (ll < nl) {
                 const long long g0 = line_base(ll);
-#pragma unroll 4
                 for (int i = tl; i < n; i += TPL) {
                     if (!IGAPW_IDX("chunk stage x", g0 + i, ntot)) continue;
-                    d[i] = make_float2(chunkstep::ld_stream(uh + g0 + i), chunkstep::ld_stream(uh + g0 + i + ntot));
+                    cp_async4(&d[i].x, uh + g0 + i);
+                    cp_async4(&d[i].y, uh + g0 + i + ntot);
                 }
             } else {
                 for (int i = tl; i < n; i += TPL) d[i] = make_float2(0.f, 0.f);
@@ -189,12 +178,12 @@ __global__ void __launch_bounds__(512) chunk_step_kernel(const AxisStepArgs a) {
         const float* sh = uh + g0;
         const float* sl = sh + ntot;
         const int rsi = (int)rs;
-#pragma unroll 4
         for (int i = k; i < n; i += P) {
             float2* d = U2 + i * ust + l;
             if (l < nl) {
                 if (!IGAPW_IDX("chunk stage c", g0 + (long long)i * rs, ntot)) continue;
-                *d = make_float2(chunkstep::ld_stream(sh + i * rsi), chunkstep::ld_stream(sl + i * rsi));
+                cp_async4(&d->x, sh + i * rsi);
+                cp_async4(&d->y, sl + i * rsi);
             } else {
                 *d = make_float2(0.f, 0.f);
             }
@@ -202,6 +191,7 @@ __global__ void __launch_bounds__(512) chunk_step_kernel(const AxisStepArgs a) {
         for (int i = n + k; i < nr; i += P) U2[i * ust + l] = make_float2(0.f, 0.f);
         for (int i = np + k; i < nr; i += P) W0[i * ust + l] = 0.f;
     }
+    cp_async_wait_all();
     __syncthreads();
 
     const int r0 = k * RS;
@@ -355,9 +345,25 @@ __global__ void __launch_bounds__(512) chunk_step_kernel(const AxisStepArgs a) {
     for (int j = 0; j < RS; ++j) wl[(r0 + j) * ust] = y[j];
     __syncthreads();
 
-    // y/z lines: the update's base is the previous axes' accumulator, read
-    // in P5 (after this wait for the launch that writes it)
-    if constexpr (!XL) chunkstep::griddep_wait();
+    // the base of the update: the accumulator of the earlier axes (y/z lines),
+    // staged into the dead u tile while the residual and the correction run
+    if constexpr (!XL) {
+        chunkstep::griddep_wait();   // the previous axis' accumulator is complete
+        if (l < nl) {
+            // 32-bit row offsets from per-line pointers (a line spans < 2^31 elements)
+            const long long g0 = line_base(l) + (long long)r0 * rs;
+            const float* ah = static_cast<const float*>(a.acc) + g0;
+            const float* al = ah + ntot;
+            const int rsi = (int)rs;
+            const int R = min(RS, n - r0);   // rows of the chunk inside the line
+            for (int j = 0; j < R; ++j) {
+                if (!IGAPW_IDX("chunk base", g0 + (long long)j * rs, ntot)) continue;
+                float2* d = U2 + (r0 + j) * ust + l;
+                cp_async4(&d->x, ah + j * rsi);
+                cp_async4(&d->y, al + j * rsi);
+            }
+        }
+    }
 
     // ---- P3: rho = g - A w0 (double-float) fused with the forward sweep -------
 #pragma unroll
@@ -403,12 +409,12 @@ __global__ void __launch_bounds__(512) chunk_step_kernel(const AxisStepArgs a) {
     // ---- P5: out = base + dt (w0 + d) ------------------------------------------
     float dth, dtl;
     split_double(a.dt, dth, dtl);
+    if constexpr (!XL) cp_async_wait_all();   // own rows only: no barrier needed
     unsigned bad = 0;
     float* oh = static_cast<float*>((MODE == 0 || MODE == 1) ? a.acc : a.u_out);
     const long long gl0 = (!XL && l < nl) ? line_base(l) : 0;
     // this thread's first row of the line (y/z lines), advanced row by row
     float* oq = oh + gl0 + (long long)r0 * rs;
-    const float* bq = static_cast<const float*>(a.acc) + gl0 + (long long)r0 * rs;
     const long long rsl = rs;
 #pragma unroll
     for (int j = 0; j < RS; ++j) {
@@ -419,14 +425,7 @@ __global__ void __launch_bounds__(512) chunk_step_kernel(const AxisStepArgs a) {
         pe = fmaf(dtl, w0, pe);
         pe = fmaf(dth, y[j], pe);
         float2* bp = U2 + l * lst + i * ust;
-        float2 b;
-        if constexpr (XL) {
-            b = *bp;   // u, staged
-        } else {
-            b = (l < nl && i < n) ? make_float2(chunkstep::ld_stream(bq), chunkstep::ld_stream(bq + ntot))
-                                  : make_float2(0.f, 0.f);
-            bq += rsl;
-        }
+        const float2 b = *bp;
         float s, e;
         two_sum(b.x, ph, s, e);
         float hi, lo;
