@@ -515,7 +515,8 @@ def measure_serving(requests=2000, seed=6, budget=120 * 10 ** 9):
     64^2..1024^2 / 30% 3D 32^3..160^3, p in {2,3}, FP64 / FP32 pairs) through
     the continuous-batching server: slots for every shape created first
     (resident tables, factors and pencils), capacity from a closed-loop run of
-    300 requests, then `requests` Poisson arrivals at 80% of that capacity.
+    600 requests of the same mix, then `requests` Poisson arrivals at 80% of
+    that capacity.
     A sample of the served results is checked against the oracle."""
     import numpy as np
     import torch
@@ -524,7 +525,9 @@ def measure_serving(requests=2000, seed=6, budget=120 * 10 ** 9):
     torch.cuda.empty_cache()        # the rows before leave cached blocks of other sizes
     srv = serve.Server(budget_bytes=budget)
     stream = serve.make_stream(requests, rate=1.0, seed=seed)
-    probe = serve.make_stream(300, rate=None, seed=seed + 1)
+    # capacity: closed loop (all at t = 0) over 600 requests drawn from the
+    # stream's own distribution (same seed), so that it measures that mix
+    probe = serve.make_stream(600, rate=None, seed=seed)
     t0 = time.perf_counter()
     srv.warm(sorted({r.shape for r in stream + probe}, key=str))
     torch.cuda.synchronize()

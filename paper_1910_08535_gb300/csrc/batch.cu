@@ -86,6 +86,7 @@ __global__ void __launch_bounds__(TX * TY) batch_source_kernel(const BInst* inst
         const DF r = df_mul(df_mul(gx.result(), gy.result()), DF{S.amp, 0.f});
         const long long e = (long long)j * I.nx + i;
         const long long nt = (long long)I.nx * I.ny;
+        if (!IGAPW_IDX("batch source out", e, nt)) continue;
         bpair[2 * I.off + e] = r.hi;
         bpair[2 * I.off + nt + e] = r.lo;
     }
@@ -125,7 +126,10 @@ __global__ void __launch_bounds__(256) batch_residual_kernel(const BInst* insts,
         for (int e = threadIdx.x; e < YH * XH; e += blockDim.x) {
             const int r = e / XH, c = e - r * XH;
             const int gy = yl + r, gx = xl + c;
-            us[r][c] = (r < nyh && c < nxh && gy < ny && gx < nx) ? u[(long long)gy * nx + gx] : 0.f;
+            us[r][c] = (r < nyh && c < nxh && gy < ny && gx < nx &&
+                        IGAPW_IDX("batch residual u", (long long)gy * nx + gx, (long long)nx * ny))
+                           ? u[(long long)gy * nx + gx]
+                           : 0.f;
         }
         __syncthreads();
         for (int e = threadIdx.x; e < TY * XH; e += blockDim.x) {
@@ -155,6 +159,7 @@ __global__ void __launch_bounds__(256) batch_residual_kernel(const BInst* insts,
             if (yy >= nyo || xx >= nxo) continue;
             const int i = x0 + xx, j = y0 + yy;
             const long long g = (long long)j * nx + i;
+            if (!IGAPW_IDX("batch residual out", g, nt)) continue;
             DFAcc acc;
             acc.s = bpair[2 * I.off + g];
             acc.c = bpair[2 * I.off + nt + g];
@@ -192,6 +197,7 @@ __global__ void __launch_bounds__(256) batch_elem_kernel(const BInst* insts, con
         for (int x = threadIdx.x; x < I.px; x += blockDim.x) {
             const long long tp = I.poff + (long long)y * I.px + x;
             const long long g = (long long)y * nx + x;
+            if (!IGAPW_IDX("batch elem row", y, I.ny) || (x < nx && !IGAPW_IDX("batch elem", g, nt))) continue;
             switch (mode) {
                 case EL_PACK_HI: t[tp] = x < nx ? bpair[2 * I.off + g] : 0.f; break;
                 case EL_PACK_F32: t[tp] = x < nx ? f32in[I.off + g] : 0.f; break;

@@ -157,22 +157,36 @@ struct AxisDev {
     ChunkDev ck;    // chunked-step tables (ck.P == 0: not built)
 };
 
+// Bounds-check record of one translation unit (debug builds).
+struct BoundsReport {
+    unsigned count;
+    long long index, limit, line;
+    const char* file;
+};
+using BoundsReader = BoundsReport (*)();
+void register_bounds_reader(BoundsReader r);   // api.cu
+
 // Status bits written by kernels (read back by igapw_sync_status).
 enum : unsigned { STATUS_NONFINITE = 1u, STATUS_SINGULAR = 2u };
 
-// Debug builds (-DIGAPW_BOUNDS_CHECK): index checks that report the first
-// out-of-range accesses with printf and make the caller skip them.  Release
+// Debug builds (-DIGAPW_BOUNDS_CHECK): index checks that skip an out-of-range
+// access and record it in a per-translation-unit counter together with the
+// first offender's index, limit and source line; igapw_sync_status reads the
+// counters of every unit and fails with IGAPW_ERR_DEVICE_STATUS.  Release
 // builds compile the checks away.
 #ifdef IGAPW_BOUNDS_CHECK
-static __device__ int g_igapw_nbad;
-__device__ __forceinline__ bool igapw_check_idx(const char* site, long long i, long long lim) {
+static __device__ unsigned g_igapw_nbad;
+static __device__ long long g_igapw_first[3];
+__device__ __forceinline__ bool igapw_check_idx(int line, long long i, long long lim) {
     if (i >= 0 && i < lim) return true;
-    if (atomicAdd(&g_igapw_nbad, 1) < 16)
-        printf("igapw bounds: %s index %lld limit %lld block (%d,%d) thread %d\n", site, i, lim, (int)blockIdx.x,
-               (int)blockIdx.y, (int)threadIdx.x);
+    if (atomicAdd(&g_igapw_nbad, 1u) == 0) {
+        g_igapw_first[0] = i;
+        g_igapw_first[1] = lim;
+        g_igapw_first[2] = line;
+    }
     return false;
 }
-#define IGAPW_IDX(site, i, lim) igapw_check_idx(site, (long long)(i), (long long)(lim))
+#define IGAPW_IDX(site, i, lim) igapw_check_idx(__LINE__, (long long)(i), (long long)(lim))
 #else
 #define IGAPW_IDX(site, i, lim) true
 #endif
@@ -208,3 +222,25 @@ inline void cp_async_wait_all() {}
 #endif
 
 }  // namespace igapw
+
+#if defined(IGAPW_BOUNDS_CHECK) && !defined(IGAPW_HOST_EMU)
+namespace igapw {
+// Reads and clears this translation unit's bounds-check record (host side).
+static BoundsReport igapw_read_bounds_tu() {
+    BoundsReport r{};
+    r.file = __BASE_FILE__;
+    long long f[3] = {0, 0, 0};
+    if (cudaMemcpyFromSymbol(&r.count, g_igapw_nbad, sizeof(unsigned)) != cudaSuccess) return r;
+    if (r.count) {
+        cudaMemcpyFromSymbol(f, g_igapw_first, sizeof f);
+        const unsigned zero = 0;
+        cudaMemcpyToSymbol(g_igapw_nbad, &zero, sizeof zero);
+    }
+    r.index = f[0];
+    r.limit = f[1];
+    r.line = f[2];
+    return r;
+}
+static const int igapw_bounds_registered = (register_bounds_reader(&igapw_read_bounds_tu), 0);
+}  // namespace igapw
+#endif

@@ -107,6 +107,7 @@ constexpr bool op_tables() { return MODE == MODE_OP || MODE == MODE_PK || MODE =
 // F32 with pair r, F64 with F64 r)
 template <typename CT, int MODE, int IO>
 __device__ __forceinline__ CT load_u(const ContractArgs& a, long long g) {
+    if (!IGAPW_IDX("contract load_u", g, a.ntot)) return CT{};
     if constexpr (MODE == MODE_RES || (MODE == MODE_PRES && IO == FMT_PAIR)) {
         const float v = ((const float*)a.u)[g];
         if constexpr (std::is_same<CT, double>::value) return (double)v;
@@ -121,6 +122,7 @@ __device__ __forceinline__ CT load_u(const ContractArgs& a, long long g) {
 
 template <typename CT, int MODE, int IO>
 __device__ __forceinline__ void store_r(const ContractArgs& a, long long g, CT v) {
+    if (!IGAPW_IDX("contract store_r", g, a.ntot)) return;
     if constexpr (MODE == MODE_PRES && IO == FMT_F64) {
         ((float*)a.out)[g] = (float)(((const double*)a.r)[g] - v);
     } else if constexpr (MODE == MODE_RES || MODE == MODE_PRES) {

@@ -67,6 +67,7 @@ __global__ void __launch_bounds__(256) source_pass_kernel(const void* in, void* 
         const int q = ps + w;
         if (q >= Qa) break;
         const long long gi = (o * Qa + q) * Ni + x;
+        if (!IGAPW_IDX("source pass in", gi, No * (long long)Qa * Ni)) continue;
         CT v;
         if constexpr (std::is_same<CT, double>::value) {
             v = IN_F32 ? (double)((const float*)in)[gi] : ((const double*)in)[gi];
@@ -128,6 +129,7 @@ __global__ void __launch_bounds__(256) source_pw_kernel(const SourceArgs a) {
             for (int c = 0; c < wx; ++c) {
                 const int qx = psx + c;
                 if (qx >= Qx) break;
+                if (!IGAPW_IDX("source pw f", row + qx, (long long)Qx * Qy * a.q[2])) continue;
                 const CT tw = tab<CT>(X.TW, i * wx + c);
                 if constexpr (std::is_same<CT, double>::value) {
                     const double fv = IN_F32 ? (double)((const float*)a.f)[row + qx] : ((const double*)a.f)[row + qx];
@@ -141,6 +143,7 @@ __global__ void __launch_bounds__(256) source_pw_kernel(const SourceArgs a) {
         }
     }
     const CT r = acc.result();
+    if (!IGAPW_IDX("source out", e, a.ntot)) return;
     if constexpr (std::is_same<CT, double>::value) {
         ((double*)a.out)[e] = r;
     } else {
@@ -255,7 +258,8 @@ __global__ void __launch_bounds__(256) source_pw_rows_kernel(const SourceArgs a)
                 const long long row = ((long long)qz * Qy + (psy + by)) * Qx + psx;
 #pragma unroll
                 for (int c = 0; c < MAXW; ++c)
-                    fv[by][c] = (by < cy && c < cx) ? ((const FT*)a.f)[row + c] : FT(0);
+                    fv[by][c] = (by < cy && c < cx && IGAPW_IDX("source rows f", row + c, (long long)Qx * Qy * a.q[2]))
+                                    ? ((const FT*)a.f)[row + c] : FT(0);
             }
 #pragma unroll
             for (int by = 0; by < MAXW; ++by) {
@@ -275,6 +279,7 @@ __global__ void __launch_bounds__(256) source_pw_rows_kernel(const SourceArgs a)
             }
         }
         const CT r = acc.result();
+        if (!IGAPW_IDX("source rows out", e, a.ntot)) continue;
         if constexpr (std::is_same<CT, double>::value) {
             ((double*)a.out)[e] = r;
         } else {
@@ -320,7 +325,7 @@ __global__ void __launch_bounds__(256) source_pw_xrow_kernel(const SourceArgs a)
 #pragma unroll
             for (int c = 0; c < MAXW; ++c) {
                 const int qx = psx + c;
-                const bool in = c < wx && qx < Qx;
+                const bool in = c < wx && qx < Qx && IGAPW_IDX("source xrow f", row + qx, (long long)Qx * Qy * Qz);
                 if constexpr (IN_F32) fv[c] = in ? ((const float*)a.f)[row + qx] : 0.f;
                 else dv[c] = in ? ((const double*)a.f)[row + qx] : 0.0;
             }
@@ -338,6 +343,7 @@ __global__ void __launch_bounds__(256) source_pw_xrow_kernel(const SourceArgs a)
         }
     }
     const CT r = acc.result();
+    if (!IGAPW_IDX("source out", e, a.ntot)) return;
     if constexpr (std::is_same<CT, double>::value) {
         ((double*)a.out)[e] = r;
     } else {
