@@ -462,11 +462,12 @@ def measure_ladder(stream, flush, hbm_peak, reps=5):
 
 def measure_poisson(stream, flush, reps=10):
     """Row f1 (multi-D Poisson, Sec. 4.3 problem): 2D, 1024^2 elements, cubic
-    PW tests, solve K u = b by fast diagonalisation (FP32 GEMM transforms per
+    PW tests, solve K u = b by fast diagonalisation (dense transforms per
     axis) inside iterative refinement; FP32 pairs (1 correction) and FP64 (3
-    corrections), plain FP32 GEMMs and BF16x9 tensor-pipe emulation.  The
-    GEMM work of one transform application is 2 x sum_a 2 n_a N flops (W's
-    then V's; N coefficients)."""
+    corrections); transforms on the library's tcgen05 split-TF32 kernel (the
+    default), on cuBLAS FP32 GEMMs and on cuBLAS BF16x9 emulation.  The GEMM
+    work of one transform application is 2 x sum_a 2 n_a N flops (W's then
+    V's; N coefficients; counted once per FP32 product)."""
     import numpy as np
     import torch
     from paper_1910_08535_gb300 import igapw, workloads
@@ -474,7 +475,8 @@ def measure_poisson(stream, flush, reps=10):
     ne, p = 1024, 3
     res = {}
     for prec in ('fp32r', 'fp64'):
-        for tag, flags in (('fp32_gemm', 0), ('bf16x9', igapw.IGAPW_FLAG_FDM_BF16X9)):
+        for tag, flags in (('tc_split_tf32', 0), ('cublas_fp32', igapw.IGAPW_FLAG_FDM_CUBLAS),
+                           ('cublas_bf16x9', igapw.IGAPW_FLAG_FDM_BF16X9)):
             with torch.cuda.stream(stream):
                 t_create = time.perf_counter()
                 c = Context(dim=2, n_elem=ne, degree=p, nq=p + 1, test='pw', precision=prec, op='poisson',
@@ -576,7 +578,9 @@ def measure_batch(stream, count=512, seed=0, reps=10):
     """Row f2 (batched 2D Poisson, 512 uneven instances): N log-uniform on 16
     rungs in [32, 512] per axis, p in {2, 3}, PW tests, FP32 pairs with one
     refinement; manufactured sources amp sin(k1 pi x) sin(k2 pi y), k uniform in
-    1..4.  Times the fused source kernel and the graph-captured batch solve."""
+    1..4.  Times the fused source kernel and the graph-captured batch solve
+    (grouped transforms on the tensor-core kernel; the cuBLAS grouped GEMMs
+    beside it)."""
     import numpy as np
     import torch
     from paper_1910_08535_gb300 import workloads
@@ -591,11 +595,17 @@ def measure_batch(stream, count=512, seed=0, reps=10):
         t_create = time.perf_counter() - t0
         t_src = _time_events(stream, lambda: bt.source_sine(par), reps)
         t_solve = _time_events(stream, bt.solve, reps)
+        bt.sync_status()
+        bc = Batch(shapes, stream=stream, gemm='cublas')
+        bc.source_sine(par)
+        t_solve_cublas = _time_events(stream, bc.solve, reps)
+        bc.close()
     dof = sum((a + p) * (b + p) for a, b, p in shapes)
     flops = sum(2 * 2 * 2 * ((a + p) + (b + p)) * (a + p) * (b + p) for a, b, p in shapes)
     out = {'instances': count, 'dof': dof, 'create_s': t_create, 'tiles_source_residual': bt.tiles(),
            'source_us': t_src * 1e6, 'solve_us': t_solve * 1e6, 'instances_per_s': count / t_solve,
            'dof_per_s': dof / t_solve, 'gemm_tflops': flops / t_solve / 1e12,
+           'solve_us_cublas_grouped': t_solve_cublas * 1e6,
            'params': par, 'batch': bt}
     return out
 

@@ -61,7 +61,7 @@ extern "C" {
 #define IGAPW_ERR_OOM           -3  /* device or host allocation failed             */
 #define IGAPW_ERR_CUDA          -4  /* a CUDA runtime call failed                   */
 #define IGAPW_ERR_DEVICE_STATUS -5  /* a kernel reported a bad value (NaN / Inf)    */
-#define IGAPW_ERR_TIMEOUT       -6  /* reserved: a bounded device wait gave up      */
+#define IGAPW_ERR_TIMEOUT       -6  /* a bounded device wait gave up                */
 
 /* ---- descriptor enums --------------------------------------------------- */
 #define IGAPW_GALERKIN      0  /* B-spline tests (comparator)                       */
@@ -90,10 +90,13 @@ extern "C" {
                                        tested RHS T(u + dt Lap u), then the Kronecker
                                        mass solve; default is the split form (see
                                        igapw_step)                                    */
-#define IGAPW_FLAG_FDM_BF16X9 4     /* 2D/3D POISSON: run the FP32 transforms of the
-                                       solve as cuBLAS FP32 GEMMs emulated with three
-                                       bf16 terms on the tensor pipe (BF16x9) instead
-                                       of plain FP32 GEMMs                            */
+#define IGAPW_FLAG_FDM_BF16X9 4     /* 2D/3D POISSON: run the transforms of the solve
+                                       as cuBLAS FP32 GEMMs emulated with bf16 terms
+                                       on the tensor pipe (BF16x9) instead of the
+                                       library's tcgen05 split-TF32 kernel            */
+#define IGAPW_FLAG_FDM_CUBLAS 8     /* 2D/3D POISSON: run the transforms as plain
+                                       cuBLAS FP32 GEMMs (CUDA cores) instead of the
+                                       library's tcgen05 split-TF32 kernel            */
 
 #define IGAPW_MAX_DIM    3
 #define IGAPW_MAX_DEGREE 4
@@ -320,13 +323,36 @@ long long igapw_size(igapw_ctx* ctx, int* dims);
 /* Frees everything the context owns.  Synchronizes its stream first. */
 int igapw_destroy(igapw_ctx* ctx);
 
+/* ---- the dense transform kernel -------------------------------------------
+ * D(m, n) = sum_k A(m, k) B(n, k) for batch entries b = 0 .. batch-1, with
+ * A(m, k) = A[b bA + m sAm + k sAk], B(n, k) = B[b bB + n sBn + k sBk],
+ * D(m, n) = D[b bD + m sDm + n sDn] (device pointers, FP32, strides in
+ * elements): the split-TF32 tcgen05 GEMM that runs the fast-diagonalisation
+ * transforms of the POISSON solve (each FP32 operand split into a TF32 high
+ * part and an FP32 low part, three tensor-core products summed in FP32;
+ * relative error about 2^-21 per product; each 32-wide K chunk summed in
+ * tensor memory, the chunks summed in FP32 registers).  pre = 1 (2): A (B) is split once
+ * into shared-memory tiles before the product and streamed by bulk copies,
+ * the path the solver takes for its constant matrices; a pre-split operand
+ * must have batch stride 0 when batch > 1.  bn: tile width (0, 64, 96 or
+ * 128; 0 lets the cost model choose).  Synchronous on cuda_stream (NULL:
+ * the legacy default stream).  IGAPW_ERR_TIMEOUT if a pipeline wait of the
+ * kernel timed out; the message is in igapw_last_error(NULL).  Allocates a
+ * temporary buffer when pre != 0. */
+int igapw_tc_gemm(int M, int N, int K, int batch, const float* A, long long sAm, long long sAk, long long bA,
+                  const float* B, long long sBn, long long sBk, long long bB, float* D, long long sDm, long long sDn,
+                  long long bD, int pre, int bn, void* cuda_stream);
+
 /* ---- batched 2D Poisson over many uneven instances ----------------------
  * The problem of Sec. 4.3 (-Lap u = f, zero Dirichlet rows, Eq. (7) tested
  * with PW cells or B-splines) for `count` independent 2D instances of
  * different sizes and degrees, FP32 pairs with one refinement step (as
  * igapw_solve on a 2D POISSON context).  Each stage runs for all instances
  * in one launch: the source RHS (a persistent kernel over a work queue of
- * instance tiles), the fast-diagonalisation transforms (grouped GEMMs), the
+ * instance tiles), the fast-diagonalisation transforms (grouped GEMMs on the
+ * library's tensor-core kernel, each instance's x and y matrices split once
+ * into hi/lo tiles at creation; plain cuBLAS grouped FP32 GEMMs instead when
+ * descs[0].flags has IGAPW_FLAG_FDM_CUBLAS), the
  * double-float residual (persistent kernels, one per window width) and the
  * elementwise updates; the solve is captured once into a CUDA graph.  The
  * batch owns the instances' RHS and solution tensors (pair layout, see
@@ -351,6 +377,12 @@ int igapw_batch_source_sine(igapw_batch* b, const double* params);
  * igapw_batch_source_sine or written through igapw_batch_tensor).
  * Asynchronous on the batch stream (one graph launch). */
 int igapw_batch_solve(igapw_batch* b);
+
+/* Synchronizes the batch stream and reads the batch's device status word:
+ * IGAPW_ERR_TIMEOUT if a tensor-core GEMM gave up waiting for its pipeline
+ * (its results are then invalid), else IGAPW_OK (or the CUDA error of the
+ * stream). */
+int igapw_batch_sync_status(igapw_batch* b);
 
 /* Device pointer of instance i's RHS (which = 0) or solution (which = 1):
  * a pair tensor of 2 * n_total floats owned by the batch. */

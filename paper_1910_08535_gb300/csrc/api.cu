@@ -8,6 +8,7 @@
 #include "../../include/igapw.h"
 #include "kernels.h"
 #include "poisson.h"
+#include "tcgemm.cuh"
 #include "setup.h"
 
 using namespace igapw;
@@ -553,7 +554,10 @@ int build_fdm(igapw_ctx* c) {
     c->fdm = new (std::nothrow) FdmState();
     if (!c->fdm) return fail(c, IGAPW_ERR_OOM, "host allocation failed");
     std::string err;
-    const int rc = fdm_build(*c->fdm, c->dim, in, fr, (c->d.flags & IGAPW_FLAG_FDM_BF16X9) != 0, c->stream, err);
+    const int gemm = (c->d.flags & IGAPW_FLAG_FDM_BF16X9)   ? FDM_GEMM_BF16X9
+                     : (c->d.flags & IGAPW_FLAG_FDM_CUBLAS) ? FDM_GEMM_CUBLAS
+                                                            : FDM_GEMM_TC;
+    const int rc = fdm_build(*c->fdm, c->dim, in, fr, gemm, c->status, c->stream, err);
     if (rc) return fail(c, rc, "Poisson set-up: " + err);
     return IGAPW_OK;
 }
@@ -968,7 +972,42 @@ int igapw_sync_status(igapw_ctx* c) {
         unsigned z = 0;
         CKC(c, cudaMemcpy(c->status, &z, sizeof z, cudaMemcpyHostToDevice));
         if (st & STATUS_NONFINITE) return fail(c, IGAPW_ERR_DEVICE_STATUS, "a solve produced a non-finite value");
+        if (st & STATUS_TC_TIMEOUT)
+            return fail(c, IGAPW_ERR_TIMEOUT, "a tensor-core transform gave up waiting for its MMAs");
         return fail(c, IGAPW_ERR_DEVICE_STATUS, "device status " + std::to_string(st));
+    }
+    return IGAPW_OK;
+}
+
+int igapw_tc_gemm(int M, int N, int K, int batch, const float* A, long long sAm, long long sAk, long long bA,
+                  const float* B, long long sBn, long long sBk, long long bB, float* D, long long sDm, long long sDn,
+                  long long bD, int pre, int bn, void* cuda_stream) {
+    g_create_error.clear();
+    if (M <= 0 || N <= 0 || K <= 0 || batch <= 0 || !A || !B || !D || pre < 0 || pre > 2 ||
+        (bn != 0 && bn != 64 && bn != 96 && bn != 128)) {
+        g_create_error = "igapw_tc_gemm: need M, N, K, batch >= 1, non-NULL A, B, D, pre in {0, 1, 2}, bn in {0, 64, 96, "
+                         "128}";
+        return IGAPW_ERR_ARG;
+    }
+    if (pre != 0 && batch != 1 && (pre == 1 ? bA : bB) != 0) {
+        g_create_error = "igapw_tc_gemm: a pre-split operand is one matrix for every batch entry (its batch stride 0)";
+        return IGAPW_ERR_ARG;
+    }
+    TcGemmArgs g{};
+    g.M = M; g.N = N; g.K = K; g.batch = batch;
+    g.A = A; g.sAm = sAm; g.sAk = sAk; g.bA = bA;
+    g.B = B; g.sBn = sBn; g.sBk = sBk; g.bB = bB;
+    g.D = D; g.sDm = sDm; g.sDn = sDn; g.bD = bD;
+    g.pre = pre;
+    g.bn = bn;
+    const cudaError_t e = tc_gemm_entry(g, (cudaStream_t)cuda_stream);
+    if (e == cudaErrorLaunchTimeout) {
+        g_create_error = "igapw_tc_gemm: a pipeline wait of the kernel timed out";
+        return IGAPW_ERR_TIMEOUT;
+    }
+    if (e != cudaSuccess) {
+        g_create_error = std::string("igapw_tc_gemm: ") + cudaGetErrorString(e);
+        return e == cudaErrorInvalidValue ? IGAPW_ERR_ARG : IGAPW_ERR_CUDA;
     }
     return IGAPW_OK;
 }

@@ -27,6 +27,7 @@
 #include "common.cuh"
 #include "kernels.h"
 #include "poisson.h"
+#include "tcgemm.cuh"
 
 namespace igapw {
 namespace {
@@ -250,7 +251,15 @@ struct igapw_batch {
     std::vector<int4*> ritems[3];
     std::vector<int> rnitems[3];
     int src_tile = 0, res_tile = 0;
-    // grouped GEMMs
+    // grouped GEMMs on the tensor cores (tcgemm.cuh): per stage the GEMM
+    // descriptions, the tile work list, the tile width and which operand is
+    // pre-split (the instance's W / V matrix)
+    bool tc = true;
+    TcGemmArgs* tg[4] = {nullptr, nullptr, nullptr, nullptr};
+    int4* titems[4] = {nullptr, nullptr, nullptr, nullptr};
+    int tn[4] = {0, 0, 0, 0}, tbn[4] = {0, 0, 0, 0}, tpre[4] = {0, 0, 0, 0};
+    unsigned* status = nullptr;  // device status word (tensor-core wait timeouts)
+    // grouped GEMMs on cuBLAS (IGAPW_FLAG_FDM_CUBLAS)
     cublasHandle_t blas = nullptr;
     void* blas_ws = nullptr;
     std::vector<int> gm[4], gn[4], gk[4], glda[4], gldb[4], gldc[4], gsize;
@@ -367,6 +376,10 @@ cudaError_t elem(igapw_batch* b, int mode, const float* f32in) {
 }
 
 int gemm_stage(igapw_batch* b, int s) {
+    if (b->tc) {
+        BCK(b, launch_tc_gemm_grouped(b->tg[s], b->titems[s], b->tn[s], b->tbn[s], b->tpre[s], b->stream));
+        return IGAPW_OK;
+    }
     BBL(b, cublasSgemmGroupedBatched(b->blas, b->gta[s].data(), b->gtb[s].data(), b->gm[s].data(), b->gn[s].data(),
                                      b->gk[s].data(), b->galpha.data(), b->gA[s], b->glda[s].data(), b->gB[s],
                                      b->gldb[s].data(), b->gbeta.data(), b->gC[s], b->gldc[s].data(), b->count,
@@ -540,6 +553,51 @@ int build(igapw_batch* b, const igapw_desc* descs) {
         BCK(b, bupload(b, &b->gB[s], B[s]));
         BCK(b, bupload(b, &b->gC[s], C[s]));
     }
+    // the same GEMMs on the tensor cores: x stages take the x matrix as A
+    // (pre-split, tile rows 128), y stages the y matrix as B (pre-split with
+    // the y stages' common tile width)
+    b->tc = !(descs[0].flags & IGAPW_FLAG_FDM_CUBLAS);
+    if (b->tc) {
+        BCK(b, balloc(b, &b->status, 1));
+        BCK(b, cudaMemsetAsync(b->status, 0, sizeof(unsigned), b->stream));
+        std::vector<TcGemmArgs> G[4];
+        for (int i = 0; i < b->count; ++i) {
+            for (int s = 0; s < 4; ++s) {
+                TcGemmArgs g{};
+                g.M = b->gm[s][i]; g.N = b->gn[s][i]; g.K = b->gk[s][i]; g.batch = 1;
+                g.A = A[s][i]; g.sAm = 1; g.sAk = b->glda[s][i];
+                if (b->gtb[s][i] == CUBLAS_OP_N) { g.B = B[s][i]; g.sBn = b->gldb[s][i]; g.sBk = 1; }
+                else { g.B = B[s][i]; g.sBn = 1; g.sBk = b->gldb[s][i]; }
+                g.D = C[s][i]; g.sDm = 1; g.sDn = b->gldc[s][i];
+                g.status = b->status;
+                G[s].push_back(g);
+            }
+        }
+        for (int s = 0; s < 4; ++s) {
+            const bool xstage = (s % 2) == 0;
+            b->tpre[s] = xstage ? 1 : 2;
+            b->tbn[s] = tc_pick_width(G[s].data(), (int)G[s].size(), b->sms);
+            for (auto& g : G[s]) {
+                const int R = xstage ? tc::BM : b->tbn[s];
+                const int rows = xstage ? g.M : g.N;
+                float* pre = nullptr;
+                BCK(b, balloc(b, &pre, (size_t)tc_presplit_floats(rows, g.K, R)));
+                if (xstage) {
+                    BCK(b, launch_tc_presplit(g.A, g.sAm, g.sAk, rows, g.K, R, pre, b->stream));
+                    g.A = pre;
+                } else {
+                    BCK(b, launch_tc_presplit(g.B, g.sBn, g.sBk, rows, g.K, R, pre, b->stream));
+                    g.B = pre;
+                }
+                g.pre = b->tpre[s];
+                g.bn = b->tbn[s];
+            }
+            const std::vector<int4> items = tc_group_items(G[s], b->tbn[s]);
+            b->tn[s] = (int)items.size();
+            BCK(b, bupload(b, &b->tg[s], G[s]));
+            BCK(b, bupload(b, &b->titems[s], items));
+        }
+    }
     // tile autotuning on the batch itself (zero inputs)
     BCK(b, cudaMemsetAsync(b->b, 0, 2 * b->total * sizeof(float), b->stream));
     BCK(b, cudaMemsetAsync(b->u0, 0, b->total * sizeof(float), b->stream));
@@ -613,6 +671,17 @@ int igapw_batch_solve(igapw_batch* b) {
         BCK(b, e);
     }
     BCK(b, cudaGraphLaunch(b->graph, b->stream));
+    return IGAPW_OK;
+}
+
+int igapw_batch_sync_status(igapw_batch* b) {
+    if (!b) return bfail(nullptr, IGAPW_ERR_ARG, "batch is NULL");
+    BCK(b, cudaStreamSynchronize(b->stream));
+    if (!b->status) return IGAPW_OK;
+    unsigned st = 0;
+    BCK(b, cudaMemcpy(&st, b->status, sizeof st, cudaMemcpyDeviceToHost));
+    if (st & STATUS_TC_TIMEOUT)
+        return bfail(b, IGAPW_ERR_TIMEOUT, "a tensor-core GEMM of the batch solve timed out waiting for its pipeline");
     return IGAPW_OK;
 }
 

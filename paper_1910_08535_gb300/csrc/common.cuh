@@ -167,7 +167,7 @@ using BoundsReader = BoundsReport (*)();
 void register_bounds_reader(BoundsReader r);   // api.cu
 
 // Status bits written by kernels (read back by igapw_sync_status).
-enum : unsigned { STATUS_NONFINITE = 1u, STATUS_SINGULAR = 2u };
+enum : unsigned { STATUS_NONFINITE = 1u, STATUS_SINGULAR = 2u, STATUS_TC_TIMEOUT = 4u };
 
 // Debug builds (-DIGAPW_BOUNDS_CHECK): index checks that skip an out-of-range
 // access and record it in a per-translation-unit counter together with the

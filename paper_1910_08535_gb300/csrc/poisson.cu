@@ -10,8 +10,9 @@
 // With W_a = V_a^{-1} A_a^{-1},
 //   K_II^{-1} = (V_x (x) V_y (x) V_z) diag(1 / (lx + ly + lz)) (W_x (x) W_y (x) W_z),
 // i.e. d dense per-axis transforms, a diagonal scaling and d more transforms:
-// plain GEMMs over the coefficient tensor (cuBLAS), with a fused diagonal
-// kernel.  The transforms run in FP32; the operator P = diag(I, K_II^{-1}) they
+// dense GEMMs over the coefficient tensor -- by default the library's tcgen05
+// tensor-core kernel in split TF32 (tcgemm.cuh), or cuBLAS FP32 / BF16x9 by
+// flag -- with a fused diagonal kernel.  The transforms run in FP32; the operator P = diag(I, K_II^{-1}) they
 // form is applied inside iterative refinement whose residual b - K u is taken
 // by the contraction kernel in FP64 or double-float arithmetic: one correction
 // for pair tensors (FP32 + refinement), `iters` corrections for FP64 tensors.
@@ -34,6 +35,7 @@
 
 #include "contract.cuh"
 #include "poisson.h"
+#include "tcgemm.cuh"
 
 namespace igapw {
 
@@ -433,10 +435,49 @@ void cache_put(const std::string& key, const std::shared_ptr<FdmAxisData>& d) {
 
 }  // namespace
 
+// D(m, n) = sum_k A(m, k) B(n, k) of the transform along axis a: M applied
+// to the padded spectral tensor `in` (n_z, n_y, px), written to `out`.  With
+// `pre` (the matrix' tc_presplit tiles) the matrix operand is read from
+// them; without, from M (column-major, leading dimension np).
+static TcGemmArgs tc_axis_args(const FdmState& s, int a, const float* M, const float* in, float* out, const float* pre) {
+    const int px = s.px, ny = s.n[1], nz = s.n[2];
+    const int ld = s.axis[a]->np;
+    TcGemmArgs g{};
+    g.status = s.status;
+    g.batch = 1;
+    g.sDm = 1;
+    if (a == 0) {          // out(x, j) = sum_k M(x, k) in(k, j), j = (z, y)
+        g.M = px; g.N = ny * nz; g.K = px;
+        g.A = M; g.sAm = 1; g.sAk = ld;
+        g.B = in; g.sBn = px; g.sBk = 1;
+        g.D = out; g.sDn = px;
+        if (pre) { g.A = pre; g.pre = 1; }
+    } else if (a == 1) {   // per z: out(x, y) = sum_k in(x, k) M(y, k)
+        g.M = px; g.N = ny; g.K = ny; g.batch = nz;
+        g.A = in; g.sAm = 1; g.sAk = px; g.bA = (long long)px * ny;
+        g.B = M; g.sBn = 1; g.sBk = ld; g.bB = 0;
+        g.D = out; g.sDn = px; g.bD = (long long)px * ny;
+        if (pre) { g.B = pre; g.pre = 2; g.bn = s.pre_bn[a]; }
+    } else {               // out(xy, z) = sum_k in(xy, k) M(z, k)
+        g.M = px * ny; g.N = nz; g.K = nz;
+        g.A = in; g.sAm = 1; g.sAk = (long long)px * ny;
+        g.B = M; g.sBn = 1; g.sBk = ld;
+        g.D = out; g.sDn = (long long)px * ny;
+        if (pre) { g.B = pre; g.pre = 2; g.bn = s.pre_bn[a]; }
+    }
+    return g;
+}
+
 void fdm_release(FdmState& s) {
     for (int k = 0; k < 2; ++k)
         if (s.t[k]) cudaFreeAsync(s.t[k], s.stream);
     s.t[0] = s.t[1] = nullptr;
+    for (int a = 0; a < 3; ++a) {
+        for (int h = 0; h < 2; ++h)
+            if (s.pre[a][h]) cudaFreeAsync(s.pre[a][h], s.stream);
+        s.pre[a][0] = s.pre[a][1] = nullptr;
+        s.pre_role[a] = s.pre_bn[a] = 0;
+    }
     if (s.blas) cublasDestroy(s.blas);
     s.blas = nullptr;
     for (int a = 0; a < 3; ++a) {
@@ -445,11 +486,12 @@ void fdm_release(FdmState& s) {
     }
 }
 
-int fdm_build(FdmState& s, int dim, const FdmAxisInput* ax, const int* const* is_free_dev, bool tensor,
-              cudaStream_t st, std::string& err) {
+int fdm_build(FdmState& s, int dim, const FdmAxisInput* ax, const int* const* is_free_dev, int gemm,
+              unsigned* status, cudaStream_t st, std::string& err) {
     fdm_release(s);
     s.dim = dim;
-    s.tensor = tensor;
+    s.gemm = gemm;
+    s.status = status;
     s.stream = st;
     for (int a = 0; a < 3; ++a) {
         s.n[a] = a < dim ? ax[a].n : 1;
@@ -487,7 +529,26 @@ int fdm_build(FdmState& s, int dim, const FdmAxisInput* ax, const int* const* is
     }
     if (S) FDM_CUDA(cudaStreamSynchronize(S->ss));
     FDM_BLAS(cublasSetStream(s.blas, st));
-    if (tensor) {
+    if (gemm == FDM_GEMM_TC) {
+        // the constant operand of every transform, split once (gemm_axis)
+        for (int a = 0; a < dim; ++a) {
+            TcGemmArgs g = tc_axis_args(s, a, nullptr, nullptr, nullptr, nullptr);
+            const int ld = s.axis[a]->np;
+            const int role = a == 0 ? 1 : 2;
+            const int R = role == 1 ? tc::BM : tc_pick_width(&g, 1, tc_sm_count());
+            const int rows = role == 1 ? g.M : g.N;
+            const long long nf = tc_presplit_floats(rows, g.K, R);
+            for (int h = 0; h < 2; ++h) {
+                const float* Mat = h == 0 ? s.Wm[a] : s.Vm[a];
+                FDM_CUDA(cudaMallocAsync((void**)&s.pre[a][h], (size_t)nf * sizeof(float), st));
+                // x axis: A(x', k) = M[x' + k ld]; y/z axes: B(n, k) = M[n + k ld]
+                FDM_CUDA(launch_tc_presplit(Mat, 1, ld, rows, g.K, R, s.pre[a][h], st));
+            }
+            s.pre_role[a] = role;
+            s.pre_bn[a] = role == 2 ? R : 0;
+        }
+    }
+    if (gemm == FDM_GEMM_BF16X9) {
         FDM_BLAS(cublasSetMathMode(s.blas, CUBLAS_FP32_EMULATED_BF16X9_MATH));
         FDM_BLAS(cublasSetEmulationStrategy(s.blas, CUBLAS_EMULATION_STRATEGY_EAGER));
     }
@@ -501,8 +562,15 @@ namespace {
 int gemm_axis(FdmState& s, int a, const float* M, const float* in, float* out, std::string& err) {
     const int px = s.px, ny = s.n[1], nz = s.n[2];
     const int ld = s.axis[a]->np;   // padded leading dimension of M
+    if (s.gemm == FDM_GEMM_TC) {
+        // the same products as the cuBLAS calls below, with the axis matrix
+        // taken from its pre-split tiles
+        TcGemmArgs g = tc_axis_args(s, a, M, in, out, s.pre[a][M == s.Wm[a] ? 0 : 1]);
+        FDM_CUDA(launch_tc_gemm(g, s.stream_now));
+        return 0;
+    }
     const float one = 1.f, zero = 0.f;
-    const cublasComputeType_t ct = s.tensor ? CUBLAS_COMPUTE_32F_EMULATED_16BFX9 : CUBLAS_COMPUTE_32F;
+    const cublasComputeType_t ct = s.gemm == FDM_GEMM_BF16X9 ? CUBLAS_COMPUTE_32F_EMULATED_16BFX9 : CUBLAS_COMPUTE_32F;
     if (a == 0) {
         FDM_BLAS(cublasGemmEx(s.blas, CUBLAS_OP_N, CUBLAS_OP_N, px, ny * nz, px, &one, M, CUDA_R_32F, ld, in,
                               CUDA_R_32F, px, &zero, out, CUDA_R_32F, px, ct, CUBLAS_GEMM_DEFAULT));
@@ -554,6 +622,7 @@ int apply_fdm(FdmState& s, const Grid3& g, cudaStream_t st, std::string& err) {
 int fdm_solve(FdmState& s, const ContractArgs& ca, const void* b, void* u, bool fp64, int iters, float* rho,
               float* u0, bool pair_fp64_residual, cudaStream_t st, std::string& err) {
     FDM_BLAS(cublasSetStream(s.blas, st));
+    s.stream_now = st;
     const Grid3 g = grid_of(s, ca.ntot);
     const dim3 gd = grid_dims(g);
     const float* t = s.t[0];
@@ -599,6 +668,47 @@ int fdm_solve(FdmState& s, const ContractArgs& ca, const void* b, void* u, bool 
         FDM_CUDA(cudaGetLastError());
     }
     return 0;
+}
+
+// The tensor-core GEMM on caller buffers (igapw_tc_gemm): synchronous; a
+// pre-split operand (pre = 1: A, 2: B) is split into a temporary buffer
+// first.  Returns a CUDA error, or cudaErrorLaunchTimeout when a pipeline
+// wait of the kernel timed out.
+static __device__ unsigned g_tc_entry_status;
+
+cudaError_t tc_gemm_entry(const TcGemmArgs& in, cudaStream_t st) {
+    TcGemmArgs g = in;
+    unsigned* status = nullptr;
+    cudaError_t e = cudaGetSymbolAddress((void**)&status, g_tc_entry_status);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(status, 0, sizeof(unsigned), st);
+    if (e != cudaSuccess) return e;
+    g.status = status;
+    float* tmp = nullptr;
+    if (g.pre == 1 || g.pre == 2) {
+        if (g.batch != 1 && (g.pre == 1 ? g.bA : g.bB) != 0) return cudaErrorInvalidValue;
+        if (g.pre == 2 && g.bn == 0) g.bn = tc_pick_width(&g, 1, tc_sm_count());
+        const int R = g.pre == 1 ? tc::BM : g.bn;
+        const int rows = g.pre == 1 ? g.M : g.N;
+        e = cudaMallocAsync((void**)&tmp, (size_t)tc_presplit_floats(rows, g.K, R) * sizeof(float), st);
+        if (e != cudaSuccess) return e;
+        if (g.pre == 1) {
+            e = launch_tc_presplit(g.A, g.sAm, g.sAk, rows, g.K, R, tmp, st);
+            g.A = tmp;
+        } else {
+            e = launch_tc_presplit(g.B, g.sBn, g.sBk, rows, g.K, R, tmp, st);
+            g.B = tmp;
+        }
+    }
+    if (e == cudaSuccess) e = launch_tc_gemm(g, st);
+    if (tmp) cudaFreeAsync(tmp, st);
+    const cudaError_t e2 = cudaStreamSynchronize(st);
+    if (e == cudaSuccess) e = e2;
+    if (e != cudaSuccess) return e;
+    unsigned h = 0;
+    e = cudaMemcpy(&h, status, sizeof h, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return e;
+    return (h & STATUS_TC_TIMEOUT) ? cudaErrorLaunchTimeout : cudaSuccess;
 }
 
 }  // namespace igapw

@@ -47,13 +47,25 @@ struct FdmState {
     float* t[2] = {nullptr, nullptr};              // spectral buffers, (n_z, n_y, px) floats each
     cudaStream_t stream = nullptr;                 // stream of the buffers' allocation
     cublasHandle_t blas = nullptr;
-    bool tensor = false;                           // FP32 GEMMs emulated on the bf16 tensor pipe
+    int gemm = 0;                                  // transforms: FDM_GEMM_TC, _CUBLAS or _BF16X9
+    unsigned* status = nullptr;                    // device status word (tensor-core wait timeouts)
+    cudaStream_t stream_now = nullptr;             // stream of the solve in progress
+    // tensor-core engine: W and V of every axis split once into hi/lo
+    // shared-memory tiles (tcgemm.cuh), as the GEMM's A operand (x axis,
+    // pre_role 1) or B operand (y and z axes, pre_role 2, tile width pre_bn)
+    float* pre[3][2] = {{nullptr, nullptr}, {nullptr, nullptr}, {nullptr, nullptr}};
+    int pre_role[3] = {0, 0, 0};
+    int pre_bn[3] = {0, 0, 0};
 };
+
+// Engines of the dense per-axis transforms: the library's tcgen05 split-TF32
+// kernel (tcgemm.cuh), cuBLAS FP32 GEMMs, cuBLAS BF16x9 emulation.
+enum { FDM_GEMM_TC = 0, FDM_GEMM_CUBLAS = 1, FDM_GEMM_BF16X9 = 2 };
 
 // Builds the spectral data of every axis (FP64 LU and eigendecomposition on
 // the device, then FP32 copies).  Returns 0, or a message in err.
-int fdm_build(FdmState& s, int dim, const FdmAxisInput* ax, const int* const* is_free_dev, bool tensor,
-              cudaStream_t st, std::string& err);
+int fdm_build(FdmState& s, int dim, const FdmAxisInput* ax, const int* const* is_free_dev, int gemm,
+              unsigned* status, cudaStream_t st, std::string& err);
 void fdm_release(FdmState& s);
 
 // Poisson solve K u = b.  Scratch: rho (ntot floats) and, for pair tensors,
@@ -62,6 +74,11 @@ void fdm_release(FdmState& s);
 // refinement steps).
 int fdm_solve(FdmState& s, const ContractArgs& ca, const void* b, void* u, bool fp64, int iters, float* rho,
               float* u0, bool pair_fp64_residual, cudaStream_t st, std::string& err);
+
+// The tensor-core GEMM of the transforms on caller buffers (tcgemm.cuh;
+// synchronous; cudaErrorLaunchTimeout when a pipeline wait timed out).
+struct TcGemmArgs;
+cudaError_t tc_gemm_entry(const TcGemmArgs& g, cudaStream_t st);
 
 // r = K u (MODE_PK) or rho = r - K u (MODE_PRES) through the contraction kernel.
 cudaError_t launch_poisson_contract(const ContractArgs& a, int mode, int cmp, int io, cudaStream_t st);

@@ -21,7 +21,7 @@ IGAPW_GALERKIN, IGAPW_PWCONST, IGAPW_REFINED = 0, 1, 2
 IGAPW_BC_NONE, IGAPW_BC_DIRICHLET0 = 0, 1
 IGAPW_FP64, IGAPW_FP32_REFINE = 0, 1
 IGAPW_OP_MASS, IGAPW_OP_LAPLACE, IGAPW_OP_HEAT, IGAPW_OP_POISSON = 0, 1, 2, 3
-IGAPW_FLAG_FP64_RESIDUAL, IGAPW_FLAG_STEP_RHS_SOLVE, IGAPW_FLAG_FDM_BF16X9 = 1, 2, 4
+IGAPW_FLAG_FP64_RESIDUAL, IGAPW_FLAG_STEP_RHS_SOLVE, IGAPW_FLAG_FDM_BF16X9, IGAPW_FLAG_FDM_CUBLAS = 1, 2, 4, 8
 
 TESTS = {'galerkin': IGAPW_GALERKIN, 'pw': IGAPW_PWCONST, 'refined': IGAPW_REFINED}
 BCS = {'none': IGAPW_BC_NONE, 'dirichlet0': IGAPW_BC_DIRICHLET0}
@@ -42,7 +42,7 @@ class igapw_desc(ctypes.Structure):
                 ('neumann_axes', ctypes.c_int), ('refine', ctypes.c_int)]
 
 
-_VP, _I, _D = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+_VP, _I, _D, _LL = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_longlong
 _SIGS = {
     'igapw_create': (_I, [ctypes.POINTER(_VP), ctypes.POINTER(igapw_desc), _VP]),
     'igapw_set_knots': (_I, [_VP, _I, ctypes.POINTER(_D), _I]),
@@ -66,6 +66,8 @@ _SIGS = {
     'igapw_batch_create': (_I, [ctypes.POINTER(_VP), ctypes.POINTER(igapw_desc), _I, _VP]),
     'igapw_batch_source_sine': (_I, [_VP, ctypes.POINTER(_D)]),
     'igapw_batch_solve': (_I, [_VP]),
+    'igapw_tc_gemm': (_I, [_I, _I, _I, _I, _VP, _LL, _LL, _LL, _VP, _LL, _LL, _LL, _VP, _LL, _LL, _LL, _I, _I, _VP]),
+    'igapw_batch_sync_status': (_I, [_VP]),
     'igapw_batch_tensor': (_I, [_VP, _I, _I, ctypes.POINTER(_VP), ctypes.POINTER(ctypes.c_longlong)]),
     'igapw_batch_info': (_I, [_VP, ctypes.POINTER(_I)]),
     'igapw_batch_last_error': (ctypes.c_char_p, [_VP]),
@@ -243,6 +245,40 @@ def igapw_destroy(ctx):
     _check(load().igapw_destroy(ctx), None)
 
 
+def igapw_tc_gemm(M, N, K, batch, A, sA, bA, B, sB, bB, D, sD, bD, pre=0, bn=0, stream=None):
+    """The library's tensor-core transform GEMM on device pointers:
+    D(m, n) = sum_k A(m, k) B(n, k) per batch entry; sA = (s_m, s_k),
+    sB = (s_n, s_k), sD = (s_m, s_n) element strides.  Synchronous."""
+    _check(load().igapw_tc_gemm(M, N, K, batch, A, sA[0], sA[1], bA, B, sB[0], sB[1], bB, D, sD[0], sD[1], bD, pre, bn,
+                                _stream_handle(stream)), None)
+
+
+def tc_gemm(a, b, out=None, pre=0, bn=0):
+    """Torch convenience form: D = A @ B^T for CUDA float32 tensors A (M x K)
+    and B (N x K) of any strides (or batched, (batch, M, K) and (batch, N, K),
+    a pre-split operand shared by the batch as a 2D tensor)."""
+    import torch
+    if a.dtype != torch.float32 or b.dtype != torch.float32 or not (a.is_cuda and b.is_cuda):
+        raise IgapwError(IGAPW_ERR_ARG, 'tc_gemm: CUDA float32 tensors required')
+    batched = a.dim() == 3 or b.dim() == 3
+    batch = a.shape[0] if a.dim() == 3 else (b.shape[0] if b.dim() == 3 else 1)
+    M, K = a.shape[-2], a.shape[-1]
+    N = b.shape[-2]
+    if b.shape[-1] != K:
+        raise IgapwError(IGAPW_ERR_ARG, f'tc_gemm: inner sizes {K} and {b.shape[-1]} differ')
+    if out is None:
+        out = torch.empty((batch, M, N) if batched else (M, N), dtype=torch.float32, device=a.device)
+    sa = a.stride()
+    sb = b.stride()
+    so = out.stride()
+    bA = sa[0] if a.dim() == 3 else 0
+    bB = sb[0] if b.dim() == 3 else 0
+    bD = so[0] if out.dim() == 3 else 0
+    igapw_tc_gemm(M, N, K, batch, a.data_ptr(), sa[-2:], bA, b.data_ptr(), sb[-2:], bB, out.data_ptr(), so[-2:], bD,
+                  pre, bn, torch.cuda.current_stream())
+    return out
+
+
 def _bcheck(rc, b=None):
     if rc != IGAPW_OK:
         msg = load().igapw_batch_last_error(b)
@@ -264,6 +300,10 @@ def igapw_batch_source_sine(b, params):
 
 def igapw_batch_solve(b):
     _bcheck(load().igapw_batch_solve(b), b)
+
+
+def igapw_batch_sync_status(b):
+    _bcheck(load().igapw_batch_sync_status(b), b)
 
 
 def igapw_batch_tensor(b, i, which):
@@ -496,13 +536,18 @@ class _DevArray:
 
 class Batch:
     """Batched 2D Poisson instances (FP32 pairs): shapes is a list of
-    (n_elem_x, n_elem_y, degree) tuples; tests PW or Galerkin."""
+    (n_elem_x, n_elem_y, degree) tuples; tests PW or Galerkin.  gemm: 'tc'
+    (the library's tensor-core transforms) or 'cublas'."""
 
-    def __init__(self, shapes, test='pw', stream=None):
+    def __init__(self, shapes, test='pw', stream=None, gemm='tc'):
         import torch
+        if gemm not in ('tc', 'cublas'):
+            raise IgapwError(IGAPW_ERR_ARG, f"Batch: gemm must be 'tc' or 'cublas', not {gemm!r}")
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         self.shapes = [tuple(s) for s in shapes]
-        descs = [_desc(2, [nx, ny], p, p + 1, test, 'dirichlet0', 'fp32r', 'poisson') for nx, ny, p in self.shapes]
+        flags = IGAPW_FLAG_FDM_CUBLAS if gemm == 'cublas' else 0
+        descs = [_desc(2, [nx, ny], p, p + 1, test, 'dirichlet0', 'fp32r', 'poisson', flags)
+                 for nx, ny, p in self.shapes]
         self.handle = igapw_batch_create(descs, self.stream)
 
     def source_sine(self, params):
@@ -516,6 +561,11 @@ class Batch:
 
     def solve(self):
         igapw_batch_solve(self.handle)
+
+    def sync_status(self):
+        """Waits for the batch stream; raises IgapwError if a tensor-core GEMM
+        of a solve timed out."""
+        igapw_batch_sync_status(self.handle)
 
     def tensor(self, i, which):
         """Instance i's RHS (which = 0) or solution (1) as a torch view of shape

@@ -59,6 +59,28 @@ def test_small_batch_against_oracle_and_single(test):
         assert rel_err(u, us) < 1e-7, (sh, rel_err(u, us))
 
 
+def test_cublas_transforms_match_tensor_cores():
+    """The batch with cuBLAS grouped GEMMs and with the tensor-core grouped
+    GEMMs on the same sources: both against the oracle, and the device status
+    word clear after the solves."""
+    from paper_1910_08535_gb300.igapw import Batch
+    shapes = [(30, 20, 2), (17, 44, 3), (64, 64, 3), (9, 9, 2)]
+    par = _params(shapes, seed=4)
+    out = {}
+    for gemm in ('tc', 'cublas'):
+        bt = Batch(shapes, gemm=gemm)
+        bt.source_sine(par)
+        bt.solve()
+        bt.sync_status()
+        out[gemm] = [bt.to_numpy(i, 1) for i in range(len(shapes))]
+        bt.close()
+    for i, sh in enumerate(shapes):
+        axes, b_ref = _oracle(sh, par[i], 'pw')
+        u_ref = poisson_nd.solve(axes, b_ref)
+        for gemm in ('tc', 'cublas'):
+            assert rel_err(out[gemm][i], u_ref) < TOL['fp32r'], (gemm, sh, rel_err(out[gemm][i], u_ref))
+
+
 def test_resolve_after_rhs_update():
     """A second source and solve through the captured graph gives the new solution."""
     from paper_1910_08535_gb300.igapw import Batch
@@ -86,6 +108,7 @@ def test_full_batch_512_sampled():
     bt = Batch(shapes)
     bt.source_sine(par)
     bt.solve()
+    bt.sync_status()
     order = np.argsort([s[0] * s[1] for s in shapes])
     for i in list(order[:3]):
         axes, b_ref = _oracle(shapes[i], par[i], 'pw')

@@ -34,10 +34,12 @@ CHILD = textwrap.dedent('''
     for dim, ne, p, test in ((2, [23, 17], 2, 'pw'), (3, [11, 9, 13], 3, 'galerkin'), (3, [20, 7, 5], 3, 'pw')):
         for kind, nl in (('chunked', 32), ('chunked', 8), ('staged', 32), ('global', 8), (None, 0)):
             c = Context(dim=dim, n_elem=ne, degree=p, nq=p + 1, test=test, precision='fp32r')
+            shape = c.shape
             if kind is not None:
                 for a in range(dim):
-                    c.set_step_shape(a, kind, nl)
-            shape = c.shape
+                    # a block of x lines takes at most as many lines as there are (shape is z, y, x)
+                    nl_a = min(nl, int(np.prod(shape[:-1]))) if (a == 0 and kind != 'chunked') else nl
+                    c.set_step_shape(a, kind, nl_a)
             u0 = workloads.normal_coeffs(shape, seed=3)
             u = c.from_numpy(u0)
             dt = 0.05 / max(ne) ** 2

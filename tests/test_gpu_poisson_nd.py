@@ -3,7 +3,8 @@ Dirichlet rows) against the oracle: operator action K u, the source RHS of a
 manufactured solution, and the solve, element by element (rel-L2 <= 1e-12 in
 FP64, <= 1e-5 for FP32 pairs with refinement), on meshes spanning several
 tiles with ragged tails; right-hand sides that are non-zero on the boundary
-rows; the BF16x9 transform option; and, at the largest grids of the mixed
+rows; the cuBLAS FP32 and BF16x9 transform options beside the default
+tensor-core transforms; and, at the largest grids of the mixed
 request stream, the residual and sampled entries against the oracle."""
 import numpy as np
 import pytest
@@ -84,18 +85,28 @@ def test_boundary_rhs_nonzero(d, ne, prec):
     c.close()
 
 
+@pytest.mark.parametrize('engine', ['bf16x9', 'cublas'])
+@pytest.mark.parametrize('d,ne', [(2, [40, 33]), (3, [9, 12, 7])])
 @pytest.mark.parametrize('prec', ['fp64', 'fp32r'])
-def test_bf16x9_transforms(prec):
+def test_transform_engines(engine, d, ne, prec):
+    """The cuBLAS transform options against the oracle and against the
+    default tensor-core transforms on the same right-hand side."""
     from paper_1910_08535_gb300 import igapw, workloads
-    d, ne, p = 2, [40, 33], 3
-    c = _ctx(dim=d, n_elem=ne, degree=p, nq=p + 1, test='pw', precision=prec, flags=igapw.IGAPW_FLAG_FDM_BF16X9)
+    p = 3
+    flag = igapw.IGAPW_FLAG_FDM_BF16X9 if engine == 'bf16x9' else igapw.IGAPW_FLAG_FDM_CUBLAS
+    c = _ctx(dim=d, n_elem=ne, degree=p, nq=p + 1, test='pw', precision=prec, flags=flag)
+    ct = _ctx(dim=d, n_elem=ne, degree=p, nq=p + 1, test='pw', precision=prec)
     axes = oracle_axes(d, ne, p, p + 1, 'pw', 'dirichlet0')
     b = workloads.uniform_coeffs(c.shape, seed=8)
     sol = c.to_numpy(c.solve(c.from_numpy(b)))
+    sol_tc = ct.to_numpy(ct.solve(ct.from_numpy(b)))
     ref = poisson_nd.solve(axes, b, sparse=True)
     assert rel_err(sol, ref) < TOL[prec], rel_err(sol, ref)
+    assert rel_err(sol_tc, ref) < TOL[prec], rel_err(sol_tc, ref)
     c.sync()
+    ct.sync()
     c.close()
+    ct.close()
 
 
 @pytest.mark.parametrize('test', ['pw', 'galerkin'])
