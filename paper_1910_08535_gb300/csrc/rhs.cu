@@ -247,6 +247,8 @@ __global__ void __launch_bounds__(256) source_pw_rows_kernel(const SourceArgs a)
         const long long e = (long long)k * plane + pe;
         const int wz = a.dim >= 3 ? a.ax[2].wq : 1, psz = a.dim >= 3 ? a.ax[2].pstart[k] : 0;
         const int cz = a.dim >= 3 ? a.ax[2].pcount[k] : 1;
+        // b = sum_z tz (sum_y ty (sum_x tx f)): the x sums of the sample rows,
+        // weighted by ty into a y sum per z point, weighted by tz into b
         Acc<CT> acc;
         acc.init();
         for (int az = 0; az < cz; ++az) {
@@ -256,11 +258,33 @@ __global__ void __launch_bounds__(256) source_pw_rows_kernel(const SourceArgs a)
 #pragma unroll
             for (int by = 0; by < MAXW; ++by) {
                 const long long row = ((long long)qz * Qy + (psy + by)) * Qx + psx;
+                if constexpr (MAXW == 2 && IN_F32 != 0) {
+                    // a 2-point cell row as one 8-byte load where it is aligned
+                    fv[by][0] = fv[by][1] = FT(0);
+                    if (by < cy) {
+                        if (cx == 2 && (row & 1) == 0 &&
+                            IGAPW_IDX("source rows f", row + 1, (long long)Qx * Qy * a.q[2])) {
+                            const float2 v = __ldg(reinterpret_cast<const float2*>((const float*)a.f + row));
+                            fv[by][0] = v.x;
+                            fv[by][1] = v.y;
+                        } else {
 #pragma unroll
-                for (int c = 0; c < MAXW; ++c)
-                    fv[by][c] = (by < cy && c < cx && IGAPW_IDX("source rows f", row + c, (long long)Qx * Qy * a.q[2]))
-                                    ? ((const FT*)a.f)[row + c] : FT(0);
+                            for (int c = 0; c < 2; ++c)
+                                if (c < cx && IGAPW_IDX("source rows f", row + c, (long long)Qx * Qy * a.q[2]))
+                                    fv[by][c] = ((const FT*)a.f)[row + c];
+                        }
+                    }
+                } else {
+#pragma unroll
+                    for (int c = 0; c < MAXW; ++c)
+                        fv[by][c] = (by < cy && c < cx &&
+                                     IGAPW_IDX("source rows f", row + c, (long long)Qx * Qy * a.q[2]))
+                                        ? ((const FT*)a.f)[row + c]
+                                        : FT(0);
+                }
             }
+            Acc<CT> sy;
+            sy.init();
 #pragma unroll
             for (int by = 0; by < MAXW; ++by) {
                 if (by < cy) {
@@ -273,10 +297,10 @@ __global__ void __launch_bounds__(256) source_pw_rows_kernel(const SourceArgs a)
                             else sx.add_prod_f(tx[c], (float)fv[by][c]);
                         }
                     }
-                    if constexpr (std::is_same<CT, double>::value) acc.add_prod(tz * ty[by], sx.result());
-                    else acc.add_prod(df_mul(tz, ty[by]), sx.result());
+                    sy.add_prod(ty[by], sx.result());
                 }
             }
+            acc.add_prod(tz, sy.result());
         }
         const CT r = acc.result();
         if (!IGAPW_IDX("source rows out", e, a.ntot)) continue;
@@ -428,7 +452,15 @@ cudaError_t launch_source(const SourceArgs& a, int fp64, cudaStream_t st) {
         for (int k = 1; k < a.dim; ++k) wmax = std::max(wmax, a.ax[k].wq);
         const long long plane = (long long)a.n[0] * a.n[1];
         if (wmax <= 4 && plane <= INT_MAX - 256) {
-            const dim3 grid((unsigned)((plane + 255) / 256), (unsigned)std::min(a.n[2], 65535));
+            // z planes per thread: enough blocks for 16 per SM, the rest of the
+            // planes walked by each thread, which loads its x and y test weights
+            // and windows once for all of them
+            const long long xb = (plane + 255) / 256;
+            int sms = 0, dev = 0;
+            cudaGetDevice(&dev);
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            const long long zb = std::max<long long>(1, (16LL * std::max(sms, 1) + xb - 1) / xb);
+            const dim3 grid((unsigned)xb, (unsigned)std::min<long long>(std::min<long long>(a.n[2], zb), 65535));
             if (wmax <= 2) {
                 if (fp64) source_pw_rows_kernel<double, 0, 2><<<grid, 256, 0, st>>>(a);
                 else source_pw_rows_kernel<DF, 1, 2><<<grid, 256, 0, st>>>(a);

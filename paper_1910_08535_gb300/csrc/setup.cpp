@@ -306,8 +306,11 @@ std::string build_axis(AxisSetup& ax, int n_elem, int p, int nq, int test, int b
         if (hi[i] - i > p || i - lo[i] > p) return "row couples beyond the +-p band";
     }
     if (ax.w > 2 * p + 1) return "window wider than 2p+1";
-    if (!set_window(ax, ax.w))
-        return "knot vector too irregular for the banded layout (row windows must step by 0 or 1)";
+    // the narrowest window width the kernels are built for (3, 5, 7 or 9)
+    const int wpad = ax.w <= 3 ? 3 : ax.w <= 5 ? 5 : ax.w <= 7 ? 7 : 9;
+    if (ax.w > 9 || !set_window(ax, wpad))
+        return "knot vector too irregular for the banded layout (row windows must step by 0 or 1 within a "
+               "window of 9 columns)";
 
     // ---- chunks of the partitioned line solve: P <= 32, length >= p -------
     set_chunks(ax, 1);
@@ -333,11 +336,22 @@ void set_chunks(AxisSetup& ax, long long lines) {
 }
 
 bool set_window(AxisSetup& ax, int wk) {
+    // Row i's window [fstart[i], fstart[i] + wk) must hold its non-zero
+    // columns [flo[i], fhi[i]], and consecutive windows step by 0 or 1 (the
+    // staged kernels load the union of a block's row windows).  Where the
+    // padded width leaves room, a window may start below its row's first
+    // non-zero column: each row takes the highest start the previous row
+    // allows, which keeps the most room for the rows after it.
     ax.fstart.assign(ax.n, 0);
     for (int i = 0; i < ax.n; ++i) {
-        ax.fstart[i] = std::max(0, std::min(ax.flo[i], ax.n - wk));
-        if (i > 0 && (ax.fstart[i] < ax.fstart[i - 1] || ax.fstart[i] > ax.fstart[i - 1] + 1)) return false;
-        if (ax.fhi[i] >= ax.fstart[i] + wk) return false;
+        int hi = std::min(ax.flo[i], std::max(0, ax.n - wk));   // a window wider than the axis starts at 0
+        int lo = std::max(0, ax.fhi[i] - wk + 1);
+        if (i > 0) {
+            hi = std::min(hi, ax.fstart[i - 1] + 1);
+            lo = std::max(lo, ax.fstart[i - 1]);
+        }
+        if (hi < lo) return false;
+        ax.fstart[i] = hi;
     }
     return true;
 }

@@ -60,11 +60,7 @@ def test_nonuniform_knots(test):
     inner = np.sort(rng.uniform(0.05, 0.95, ne - 1))
     t = np.concatenate([[0.0] * (p + 1), inner, [1.0] * (p + 1)])
     c = _ctx(dim=1, n_elem=ne, degree=p, nq=p + 1, test=test)
-    try:
-        c.set_knots(0, t)
-    except Exception as e:   # a knot vector the banded layout cannot hold is rejected, not mis-solved
-        assert 'irregular' in str(e) or 'band' in str(e)
-        return
+    c.set_knots(0, t)   # row windows start below their first non-zero column where needed
     ax = systems.Axis(ne, p, p + 1, test, knots=t)
     assert np.abs(c.assemble_1d(0, 'mass') - systems.mass(ax)).max() < 1e-13
     x, _ = c.quad_points(0)
