@@ -119,7 +119,10 @@ inline long long tc_presplit_floats(int rows, int K, int R) {
 namespace tc {
 
 constexpr unsigned kSpinLimit = 1u << 26;   // mbarrier polls before giving up
-constexpr int kGroup = 2;                    // K chunks summed in tensor memory before the register sum
+#ifndef TC_GROUP
+#define TC_GROUP 2
+#endif
+constexpr int kGroup = TC_GROUP;             // K chunks summed in tensor memory before the register sum
 #ifndef TC_PREFETCH
 #define TC_PREFETCH 1                         // K chunks whose loads are in flight in registers
 #endif
