@@ -20,6 +20,9 @@ g = C u and the banded LU solve in the precision named:
   g64_ref32   g exact, FP32 solve + one refinement with an FP32 residual
   g64_ref64   g exact, FP32 solve + one refinement with an exact residual
               (what the library's FP32-pair step does, in double-float)
+  gdiff_ref64 g in the difference form sum_w c_w (u_w - u_i) (every row of C
+              sums to zero, so the FP32 rounding of C's row sum drops out)
+              with FP32 differences, products and sums, then as g64_ref64
 """
 import sys
 import time
@@ -99,6 +102,19 @@ def main(ne, steps, test, p, dim):
             return acc
         return f
 
+    offs = sorted({j - i for i in range(n) for j in range(n) if C[i, j] != 0})
+
+    def g_diff(u, a):
+        d = u.ndim - 1 - a
+        x = np.moveaxis(u, d, 0)
+        g = np.zeros(x.shape, dtype=np.float32)
+        for o in offs:
+            rows = np.arange(max(0, -o), min(n, n - o))
+            c = C32[rows, rows + o].reshape((-1,) + (1,) * (x.ndim - 1))
+            dif = (x[rows + o] - x[rows]).astype(np.float32)
+            g[rows] = g[rows] + (c * dif).astype(np.float32)
+        return np.moveaxis(g.astype(np.float64), 0, d)
+
     def refine(resid):
         def s(g, a):
             w0 = subst(g.astype(np.float32), a, np.float32)
@@ -116,6 +132,7 @@ def main(ne, steps, test, p, dim):
         'mixed': inc(g_mixed, lambda g, a: subst(g, a, np.float32), acc32=True),
         'g64_ref32': inc(g_exact, refine('f32')),
         'g64_ref64': inc(g_exact, refine('exact')),
+        'gdiff_ref64': inc(g_diff, refine('exact')),
     }
     t = time.time()
     ref = heat.run([ax] * dim, u0, dt, steps)
