@@ -577,7 +577,14 @@ int build(igapw_batch* b, const igapw_desc* descs) {
             const bool xstage = (s % 2) == 0;
             b->tpre[s] = xstage ? 1 : 2;
             b->tbn[s] = tc_pick_width(G[s].data(), (int)G[s].size(), b->sms);
-            for (auto& g : G[s]) {
+            std::vector<CUtensorMap> maps(G[s].size());
+            std::vector<char> has_map(G[s].size(), 0);
+            for (size_t gi = 0; gi < G[s].size(); ++gi) {
+                TcGemmArgs& g = G[s][gi];
+                // the live operand (spectral buffer) by TMA: B of the x stages
+                // (tiles of the stage's width), A of the y stages (128 rows)
+                has_map[gi] = xstage ? tc_make_tmap(&maps[gi], g.B, g.sBn, g.sBk, g.bB, g.N, g.K, 1, b->tbn[s])
+                                     : tc_make_tmap(&maps[gi], g.A, g.sAm, g.sAk, g.bA, g.M, g.K, 1, tc::BM);
                 const int R = xstage ? tc::BM : b->tbn[s];
                 const int rows = xstage ? g.M : g.N;
                 float* pre = nullptr;
@@ -592,6 +599,13 @@ int build(igapw_batch* b, const igapw_desc* descs) {
                 g.pre = b->tpre[s];
                 g.bn = b->tbn[s];
             }
+            CUtensorMap* dmaps = nullptr;
+            BCK(b, bupload(b, &dmaps, maps));
+            for (size_t gi = 0; gi < G[s].size(); ++gi)
+                if (has_map[gi]) {
+                    G[s][gi].tmap = dmaps + gi;
+                    G[s][gi].tmap_rows = xstage ? b->tbn[s] : tc::BM;
+                }
             const std::vector<int4> items = tc_group_items(G[s], b->tbn[s]);
             b->tn[s] = (int)items.size();
             BCK(b, bupload(b, &b->tg[s], G[s]));

@@ -451,7 +451,7 @@ static TcGemmArgs tc_axis_args(const FdmState& s, int a, const float* M, const f
         g.A = M; g.sAm = 1; g.sAk = ld;
         g.B = in; g.sBn = px; g.sBk = 1;
         g.D = out; g.sDn = px;
-        if (pre) { g.A = pre; g.pre = 1; }
+        if (pre) { g.A = pre; g.pre = 1; g.bn = s.pre_bn[a]; }
     } else if (a == 1) {   // per z: out(x, y) = sum_k in(x, k) M(y, k)
         g.M = px; g.N = ny; g.K = ny; g.batch = nz;
         g.A = in; g.sAm = 1; g.sAk = px; g.bA = (long long)px * ny;
@@ -465,6 +465,14 @@ static TcGemmArgs tc_axis_args(const FdmState& s, int a, const float* M, const f
         g.D = out; g.sDn = (long long)px * ny;
         if (pre) { g.B = pre; g.pre = 2; g.bn = s.pre_bn[a]; }
     }
+    // the live operand's tensor map, when one was made for this input buffer
+    if (pre && s.tmaps) {
+        const int buf = in == s.t[0] ? 0 : in == s.t[1] ? 1 : -1;
+        if (buf >= 0 && s.tmap_ok[a][buf]) {
+            g.tmap = static_cast<const CUtensorMap*>(s.tmaps) + (a * 2 + buf);
+            g.tmap_rows = s.tmap_rows[a];
+        }
+    }
     return g;
 }
 
@@ -476,8 +484,11 @@ void fdm_release(FdmState& s) {
         for (int h = 0; h < 2; ++h)
             if (s.pre[a][h]) cudaFreeAsync(s.pre[a][h], s.stream);
         s.pre[a][0] = s.pre[a][1] = nullptr;
-        s.pre_role[a] = s.pre_bn[a] = 0;
+        s.pre_role[a] = s.pre_bn[a] = s.tmap_rows[a] = 0;
+        s.tmap_ok[a][0] = s.tmap_ok[a][1] = false;
     }
+    if (s.tmaps) cudaFreeAsync(s.tmaps, s.stream);
+    s.tmaps = nullptr;
     if (s.blas) cublasDestroy(s.blas);
     s.blas = nullptr;
     for (int a = 0; a < 3; ++a) {
@@ -535,7 +546,8 @@ int fdm_build(FdmState& s, int dim, const FdmAxisInput* ax, const int* const* is
             TcGemmArgs g = tc_axis_args(s, a, nullptr, nullptr, nullptr, nullptr);
             const int ld = s.axis[a]->np;
             const int role = a == 0 ? 1 : 2;
-            const int R = role == 1 ? tc::BM : tc_pick_width(&g, 1, tc_sm_count());
+            const int bn = tc_pick_width(&g, 1, tc_sm_count());
+            const int R = role == 1 ? tc::BM : bn;
             const int rows = role == 1 ? g.M : g.N;
             const long long nf = tc_presplit_floats(rows, g.K, R);
             for (int h = 0; h < 2; ++h) {
@@ -545,8 +557,25 @@ int fdm_build(FdmState& s, int dim, const FdmAxisInput* ax, const int* const* is
                 FDM_CUDA(launch_tc_presplit(Mat, 1, ld, rows, g.K, R, s.pre[a][h], st));
             }
             s.pre_role[a] = role;
-            s.pre_bn[a] = role == 2 ? R : 0;
+            s.pre_bn[a] = bn;
         }
+        // tensor maps of the spectral operand for TMA loads: the live operand
+        // is B (x axis, tiles of bn rows) or A (y/z axes, tiles of 128 rows),
+        // read from t[0] or t[1] depending on the transform's position
+        std::vector<CUtensorMap> maps(6);
+        for (int a = 0; a < dim; ++a) {
+            s.tmap_rows[a] = a == 0 ? s.pre_bn[a] : tc::BM;
+            for (int buf = 0; buf < 2; ++buf) {
+                const TcGemmArgs g = tc_axis_args(s, a, nullptr, s.t[buf], nullptr, nullptr);
+                s.tmap_ok[a][buf] = a == 0 ? tc_make_tmap(&maps[a * 2 + buf], g.B, g.sBn, g.sBk, g.bB, g.N, g.K,
+                                                         g.batch, s.tmap_rows[a])
+                                           : tc_make_tmap(&maps[a * 2 + buf], g.A, g.sAm, g.sAk, g.bA, g.M, g.K,
+                                                         g.batch, s.tmap_rows[a]);
+            }
+        }
+        FDM_CUDA(cudaMallocAsync(&s.tmaps, maps.size() * sizeof(CUtensorMap), st));
+        FDM_CUDA(cudaMemcpyAsync(s.tmaps, maps.data(), maps.size() * sizeof(CUtensorMap), cudaMemcpyHostToDevice, st));
+        FDM_CUDA(cudaStreamSynchronize(st));   // the host vector of maps goes out of scope
     }
     if (gemm == FDM_GEMM_BF16X9) {
         FDM_BLAS(cublasSetMathMode(s.blas, CUBLAS_FP32_EMULATED_BF16X9_MATH));
@@ -700,8 +729,24 @@ cudaError_t tc_gemm_entry(const TcGemmArgs& in, cudaStream_t st) {
             g.B = tmp;
         }
     }
+    // the live operand by TMA where a tensor map can describe it
+    void* dmap = nullptr;
+    if (e == cudaSuccess && (g.pre == 1 || g.pre == 2)) {
+        if (g.pre == 1 && g.bn == 0) g.bn = tc_pick_width(&g, 1, tc_sm_count());
+        CUtensorMap hm;
+        const int R = g.pre == 1 ? g.bn : tc::BM;
+        const bool ok = g.pre == 1 ? tc_make_tmap(&hm, g.B, g.sBn, g.sBk, g.bB, g.N, g.K, g.batch, R)
+                                   : tc_make_tmap(&hm, g.A, g.sAm, g.sAk, g.bA, g.M, g.K, g.batch, R);
+        if (ok) {
+            e = cudaMallocAsync(&dmap, sizeof(CUtensorMap), st);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(dmap, &hm, sizeof hm, cudaMemcpyHostToDevice, st);
+            g.tmap = static_cast<const CUtensorMap*>(dmap);
+            g.tmap_rows = R;
+        }
+    }
     if (e == cudaSuccess) e = launch_tc_gemm(g, st);
     if (tmp) cudaFreeAsync(tmp, st);
+    if (dmap) cudaFreeAsync(dmap, st);
     const cudaError_t e2 = cudaStreamSynchronize(st);
     if (e == cudaSuccess) e = e2;
     if (e != cudaSuccess) return e;

@@ -56,6 +56,11 @@ struct FdmState {
     float* pre[3][2] = {{nullptr, nullptr}, {nullptr, nullptr}, {nullptr, nullptr}};
     int pre_role[3] = {0, 0, 0};
     int pre_bn[3] = {0, 0, 0};
+    // device tensor maps of the live (spectral) operand per axis and input
+    // buffer t[0] / t[1] (null entries: per-thread loads), their tile rows
+    void* tmaps = nullptr;
+    bool tmap_ok[3][2] = {{false, false}, {false, false}, {false, false}};
+    int tmap_rows[3] = {0, 0, 0};
 };
 
 // Engines of the dense per-axis transforms: the library's tcgen05 split-TF32

@@ -40,6 +40,9 @@
 // one-step refinement two orders of magnitude in backward error.  Every wait is bounded: on a timeout the kernel
 // records STATUS_TC_TIMEOUT in the status word, lets its MMAs drain, frees its
 // tensor memory and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include <algorithm>
 #include <vector>
 
@@ -63,6 +66,13 @@ struct TcGemmArgs {
     // bB, in floats of the tile buffer) may be 0 (one matrix for all).
     int pre;
     int bn;                       // tile width (0: chosen at launch; required with pre = 2)
+    // With a pre-split operand: a tensor map (device memory, 64-byte aligned)
+    // of the other, live operand made by tc_make_tmap for tiles of tmap_rows
+    // rows; its chunks then arrive by TMA instead of per-thread loads.  The
+    // kernel uses it only when tmap_rows is its live tile's row count (BN
+    // for a live B, 128 for a live A).  Null: per-thread loads.
+    const CUtensorMap* tmap;
+    int tmap_rows;
 };
 
 namespace tc {
@@ -85,8 +95,16 @@ __host__ __device__ constexpr unsigned tc_tile_offset(int rows, int r, int k) {
     return (unsigned)(k >> 2) * tc_lbo(rows) + (unsigned)(r >> 3) * kTcSbo + (unsigned)(r & 7) * 16u +
            (unsigned)(k & 3) * 4u;
 }
-template <int BN>
-__host__ __device__ constexpr unsigned tc_stage_bytes() { return 2u * (tc_tile_bytes(tc::BM) + tc_tile_bytes(BN)); }
+// Rows of the live operand's raw tile (the operand that is not pre-split;
+// both live: no raw tile, the loaders read global memory themselves).
+template <int BN, int PRE>
+__host__ __device__ constexpr int tc_raw_rows() { return PRE == 1 ? BN : PRE == 2 ? tc::BM : 0; }
+// A stage: hi and lo tiles of A and B, then the live operand's raw FP32
+// chunk as TMA writes it (rows x 32 floats, or 32 x rows).
+template <int BN, int PRE>
+__host__ __device__ constexpr unsigned tc_stage_bytes() {
+    return 2u * (tc_tile_bytes(tc::BM) + tc_tile_bytes(BN)) + (unsigned)tc_raw_rows<BN, PRE>() * tc::BK * 4u;
+}
 
 // Tensor-memory columns allocated for the accumulators of a BN-wide tile:
 // two chunk buffers x (hi x hi, cross terms) x BN columns, as a power of two
@@ -95,18 +113,18 @@ __host__ __device__ constexpr unsigned tmem_cols(int bn) { return 4 * bn <= 256 
 
 // K chunks in flight through shared memory: as many stages as fit in 227 KB
 // next to the barriers (at most 4).
-template <int BN>
+template <int BN, int PRE>
 __host__ __device__ constexpr int tc_stages() {
-    const int fit = (int)((227u * 1024u - 256u) / tc_stage_bytes<BN>());
+    const int fit = (int)((227u * 1024u - 256u) / tc_stage_bytes<BN, PRE>());
     return fit < 4 ? fit : 4;
 }
 
 // Shared memory of one CTA: the stages, then the mbarriers (full, empty and
 // bulk-copy per stage, two chunk-accumulator pairs, done), the
 // tensor-memory address and the abort flag (256 bytes).
-template <int BN>
+template <int BN, int PRE>
 __host__ __device__ constexpr size_t tc_smem_bytes() {
-    return (size_t)tc_stages<BN>() * tc_stage_bytes<BN>() + 256;
+    return (size_t)tc_stages<BN, PRE>() * tc_stage_bytes<BN, PRE>() + 256;
 }
 
 // Floats of the pre-split form of a rows x K operand with tiles of R rows:
@@ -183,6 +201,18 @@ __device__ __forceinline__ void bulk_copy(void* dst, const void* src, unsigned b
     asm volatile(
         "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_u32(dst)),
         "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// TMA tile load (3D tensor map in global memory) into shared memory,
+// completing its bytes on the mbarrier; the innermost coordinate must be a
+// multiple of 4 floats (16 bytes).
+__device__ __forceinline__ void tma_load3(void* dst, const CUtensorMap* map, int x, int y, int z,
+                                          unsigned long long* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(
+            smem_u32(dst)),
+        "l"(map), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
         : "memory");
 }
 
@@ -302,6 +332,23 @@ struct Loader {
         }
     }
 
+    // the same items from the chunk's raw tile in shared memory as TMA wrote
+    // it: [R][32] (unit stride along K) or [32][R] (unit stride along rows)
+    __device__ __forceinline__ void fetch_raw(const float* raw, float4 (&dst)[N]) const {
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+            const int w = warp + kLoadWarps * j;
+            if (mode == MVEC) {
+                const int r = 32 * (w % (R / 32)) + 4 * (lane & 7);
+                const int k = 4 * (w / (R / 32)) + (lane >> 3);
+                dst[j] = *reinterpret_cast<const float4*>(raw + k * R + r);
+            } else {
+                const int r = 4 * w + (lane >> 3);
+                dst[j] = *reinterpret_cast<const float4*>(raw + r * BK + 4 * (lane & 7));
+            }
+        }
+    }
+
     __device__ __forceinline__ void store(const float4 (&v)[N], unsigned char* thi, unsigned char* tlo) const {
 #pragma unroll
         for (int j = 0; j < N; ++j) {
@@ -344,8 +391,10 @@ struct Loader {
 template <int BN, int PRE>
 __device__ __forceinline__ void tc_tile(const TcGemmArgs& g, const int m0, const int n0, const int b) {
     using namespace tc;
-    constexpr int NS = tc_stages<BN>();
-    constexpr unsigned STAGE = tc_stage_bytes<BN>();
+    constexpr int NS = tc_stages<BN, PRE>();
+    constexpr unsigned STAGE = tc_stage_bytes<BN, PRE>();
+    constexpr unsigned RAW = 2u * (tc_tile_bytes(BM) + tc_tile_bytes(BN));   // raw tile offset in a stage
+    constexpr int RR = tc_raw_rows<BN, PRE>();
     constexpr unsigned TA = tc_tile_bytes(BM), TB = tc_tile_bytes(BN);
     constexpr unsigned LBOA = tc_lbo(BM), LBOB = tc_lbo(BN);
     static_assert(NS >= 2 && (3 * NS + 5) * 8 + 8 <= 256, "stage count");
@@ -399,10 +448,12 @@ __device__ __forceinline__ void tc_tile(const TcGemmArgs& g, const int m0, const
         // chunk's stores are fenced and published, so the fence never waits
         // for loads in flight.
         constexpr int PD = TC_PREFETCH;
+        // the live operand by TMA (a pre-split operand and a tensor map)
+        const bool tma = PRE != 0 && g.tmap != nullptr && g.tmap_rows == RR;
         float4 ra[PD][BM / 32], rb[PD][BN / 32];
 #pragma unroll
         for (int j = 0; j < PD; ++j)
-            if (j < nchunks) {
+            if (j < nchunks && !tma) {
                 if (PRE != 1) la.fetch(j * BK, ra[j]);
                 if (PRE != 2) lb.fetch(j * BK, rb[j]);
             }
@@ -460,7 +511,17 @@ __device__ __forceinline__ void tc_tile(const TcGemmArgs& g, const int m0, const
         auto chunk = [&](int c, float4 (&xa)[BM / 32], float4 (&xb)[BN / 32]) {
             const int s = c % NS;
             unsigned char* st = tsm_raw + s * STAGE;
-            if (c >= NS && !wait_u(&empty[s], (unsigned)((c / NS) - 1) & 1u)) {
+            if (tma) {
+                // the chunk's raw tile (and the pre-split tiles) have landed;
+                // warp 9 waited for the stage to be free before it issued them
+                if (!wait_u(&txb[s], (unsigned)(c / NS) & 1u)) {
+                    ok = false;
+                    return;
+                }
+                const float* raw = reinterpret_cast<const float*>(st + RAW);
+                if (PRE == 1) lb.fetch_raw(raw, xb);
+                if (PRE == 2) la.fetch_raw(raw, xa);
+            } else if (c >= NS && !wait_u(&empty[s], (unsigned)((c / NS) - 1) & 1u)) {
                 ok = false;
                 return;
             }
@@ -469,7 +530,7 @@ __device__ __forceinline__ void tc_tile(const TcGemmArgs& g, const int m0, const
             // generic-proxy stores -> visible to the tensor core (async proxy)
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             mbar_arrive(&full[s]);
-            if (c + PD < nchunks) {
+            if (!tma && c + PD < nchunks) {
                 if (PRE != 1) la.fetch((c + PD) * BK, xa);
                 if (PRE != 2) lb.fetch((c + PD) * BK, xb);
             }
@@ -553,12 +614,25 @@ __device__ __forceinline__ void tc_tile(const TcGemmArgs& g, const int m0, const
         const float* base = (PRE == 1 ? g.A : g.B) + (long long)b * bstride +
                             (long long)rt * nchunks * 2 * (tb / 4);
         unsigned char* dst0 = tsm_raw + (PRE == 1 ? 0u : 2u * TA);
+        // the live operand's raw chunk by TMA: rows r0.. of the live operand,
+        // coordinates (k, row, batch) or (row, k, batch) after its unit stride
+        const bool tma = g.tmap != nullptr && g.tmap_rows == RR;
+        const float* lsrc = PRE == 1 ? g.B + (long long)b * g.bB : g.A + (long long)b * g.bA;
+        const int lmode = PRE == 1 ? operand_mode(lsrc, g.sBn, g.sBk) : operand_mode(lsrc, g.sAm, g.sAk);
+        const int lr0 = PRE == 1 ? n0 : m0;
+        const int lz = g.batch > 1 ? b : 0;
+        constexpr unsigned RAWB = (unsigned)RR * BK * 4u;
         int issued = 0;
         for (int c = 0; c < nchunks; ++c) {
             const int s = c % NS;
             if (c >= NS && !mbar_wait_or_abort(&empty[s], (unsigned)((c / NS) - 1) & 1u, abort_flag)) break;
-            mbar_arrive_expect_tx(&txb[s], 2u * tb);
+            mbar_arrive_expect_tx(&txb[s], 2u * tb + (tma ? RAWB : 0u));
             bulk_copy(dst0 + s * STAGE, base + (long long)c * 2 * (tb / 4), 2u * tb, &txb[s]);
+            if (tma) {
+                unsigned char* rdst = tsm_raw + s * STAGE + RAW;
+                if (lmode == MVEC) tma_load3(rdst, g.tmap, lr0, c * BK, lz, &txb[s]);
+                else tma_load3(rdst, g.tmap, c * BK, lr0, lz, &txb[s]);
+            }
             issued = c + 1;
         }
         // after an abort, let the copies in flight land before the CTA exits
@@ -625,6 +699,50 @@ inline cudaError_t launch_tc_presplit(const float* X, long long sR, long long sK
     return cudaGetLastError();
 }
 
+// Tensor map (host copy) of a live operand X(r, k) = X[b bX + r sR + k sK]
+// (rows x K, `batch` entries) for TMA loads of its chunks: R x 32 values
+// ([R][32] in shared memory when K has unit stride, [32][R] when the rows
+// do), zero outside the operand.  False when the strides or the alignment
+// allow no tensor map (the kernel then loads the operand per thread).
+inline bool tc_make_tmap(CUtensorMap* m, const float* X, long long sR, long long sK, long long bX, int rows, int K,
+                         int batch, int R) {
+    static PFN_cuTensorMapEncodeTiled_v12000 enc = nullptr;
+    if (!enc) {
+        void* fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess || !fn)
+            return false;
+        enc = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    }
+    if ((reinterpret_cast<unsigned long long>(X) & 15) != 0 || rows <= 0 || K <= 0 || R <= 0 || R > 256) return false;
+    if (batch > 1 && (bX <= 0 || (bX * 4) % 16 != 0)) return false;
+    cuuint64_t dims[3], strides[2];
+    cuuint32_t box[3], es[3] = {1, 1, 1};
+    if (sK == 1 && sR >= K && (sR * 4) % 16 == 0) {
+        dims[0] = (cuuint64_t)K;
+        dims[1] = (cuuint64_t)rows;
+        strides[0] = (cuuint64_t)(sR * 4);
+        box[0] = tc::BK;
+        box[1] = (cuuint32_t)R;
+    } else if (sR == 1 && sK >= rows && (sK * 4) % 16 == 0) {
+        dims[0] = (cuuint64_t)rows;
+        dims[1] = (cuuint64_t)K;
+        strides[0] = (cuuint64_t)(sK * 4);
+        box[0] = (cuuint32_t)R;
+        box[1] = tc::BK;
+    } else {
+        return false;
+    }
+    dims[2] = batch > 1 ? (cuuint64_t)batch : 1;
+    strides[1] = batch > 1 ? (cuuint64_t)(bX * 4) : strides[0] * dims[1];
+    box[2] = 1;
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(X), dims, strides, box, es,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 // Tile widths the kernels are built for (multiples of 32: the loaders read
 // 16 columns per tensor-memory load, per half of the warps; at most 128: the
 // four accumulator halves fill the 512 tensor-memory columns of an SM).
@@ -674,7 +792,7 @@ inline int tc_sm_count() {
 
 template <int BN, int PRE>
 inline cudaError_t launch_tc_gemm_w(const TcGemmArgs& g, cudaStream_t st) {
-    const size_t sm = tc_smem_bytes<BN>();
+    const size_t sm = tc_smem_bytes<BN, PRE>();
     cudaFuncSetAttribute(tc_gemm_kernel<BN, PRE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     const dim3 grid((unsigned)((g.M + tc::BM - 1) / tc::BM), (unsigned)((g.N + BN - 1) / BN), (unsigned)g.batch);
     tc_gemm_kernel<BN, PRE><<<grid, tc::kThreads, sm, st>>>(g);
@@ -715,7 +833,7 @@ inline std::vector<int4> tc_group_items(const std::vector<TcGemmArgs>& gs, int b
 
 template <int BN, int PRE>
 inline cudaError_t launch_tc_grouped_w(const TcGemmArgs* gs, const int4* items, int n_items, cudaStream_t st) {
-    const size_t sm = tc_smem_bytes<BN>();
+    const size_t sm = tc_smem_bytes<BN, PRE>();
     cudaFuncSetAttribute(tc_gemm_grouped_kernel<BN, PRE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     tc_gemm_grouped_kernel<BN, PRE><<<(unsigned)n_items, tc::kThreads, sm, st>>>(gs, items);
     return cudaGetLastError();
