@@ -213,6 +213,23 @@ __global__ void __launch_bounds__(256) neumann_face_kernel(const NeumannArgs a) 
     }
 }
 
+// The first term of a compensated sum: the exact product split (double-float)
+// or the product (FP64) starts the accumulator, which saves the two-sum of
+// adding it to zero.
+__device__ __forceinline__ void acc_first_prod_f(Acc<DF>& a, DF t, float v) {
+    a.s = t.hi * v;
+    float e = fmaf(t.hi, v, -a.s);
+    a.c = fmaf(t.lo, v, e);
+}
+__device__ __forceinline__ void acc_first_prod_f(Acc<double>& a, double t, double v) { a.s = t * v; }
+__device__ __forceinline__ void acc_first_prod(Acc<DF>& a, DF t, DF v) {
+    a.s = t.hi * v.hi;
+    float e = fmaf(t.hi, v.hi, -a.s);
+    e = fmaf(t.hi, v.lo, e);
+    a.c = fmaf(t.lo, v.hi, e);
+}
+__device__ __forceinline__ void acc_first_prod(Acc<double>& a, double t, double v) { a.s = t * v; }
+
 // PW source, loads batched: for every z point of the cell, the whole y-by-x
 // slab of the cell's samples (its own point counts, at most MAXW per axis) is
 // loaded before it is summed, so a thread keeps up to MAXW^2 loads in flight.
@@ -283,24 +300,29 @@ __global__ void __launch_bounds__(256) source_pw_rows_kernel(const SourceArgs a)
                                         : FT(0);
                 }
             }
+            // every sum starts from its first product (the windows hold at
+            // least one point unless the row is a Dirichlet row)
             Acc<CT> sy;
             sy.init();
 #pragma unroll
             for (int by = 0; by < MAXW; ++by) {
                 if (by < cy) {
                     Acc<CT> sx;
-                    sx.init();
+                    if (cx > 0) acc_first_prod_f(sx, tx[0], fv[by][0]);
+                    else sx.init();
 #pragma unroll
-                    for (int c = 0; c < MAXW; ++c) {
+                    for (int c = 1; c < MAXW; ++c) {
                         if (c < cx) {
                             if constexpr (std::is_same<CT, double>::value) sx.add_prod(tx[c], (double)fv[by][c]);
                             else sx.add_prod_f(tx[c], (float)fv[by][c]);
                         }
                     }
-                    sy.add_prod(ty[by], sx.result());
+                    if (by == 0) acc_first_prod(sy, ty[0], sx.result());
+                    else sy.add_prod(ty[by], sx.result());
                 }
             }
-            acc.add_prod(tz, sy.result());
+            if (az == 0) acc_first_prod(acc, tz, sy.result());
+            else acc.add_prod(tz, sy.result());
         }
         const CT r = acc.result();
         if (!IGAPW_IDX("source rows out", e, a.ntot)) continue;
