@@ -588,12 +588,12 @@ int build(igapw_batch* b, const igapw_desc* descs) {
                 const int R = xstage ? tc::BM : b->tbn[s];
                 const int rows = xstage ? g.M : g.N;
                 float* pre = nullptr;
-                BCK(b, balloc(b, &pre, (size_t)tc_presplit_floats(rows, g.K, R)));
+                BCK(b, balloc(b, &pre, (size_t)tc_presplit_floats(rows, g.K, R, !xstage)));
                 if (xstage) {
-                    BCK(b, launch_tc_presplit(g.A, g.sAm, g.sAk, rows, g.K, R, pre, b->stream));
+                    BCK(b, launch_tc_presplit(g.A, g.sAm, g.sAk, rows, g.K, R, false, pre, b->stream));
                     g.A = pre;
                 } else {
-                    BCK(b, launch_tc_presplit(g.B, g.sBn, g.sBk, rows, g.K, R, pre, b->stream));
+                    BCK(b, launch_tc_presplit(g.B, g.sBn, g.sBk, rows, g.K, R, true, pre, b->stream));
                     g.B = pre;
                 }
                 g.pre = b->tpre[s];

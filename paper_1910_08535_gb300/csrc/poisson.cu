@@ -549,12 +549,12 @@ int fdm_build(FdmState& s, int dim, const FdmAxisInput* ax, const int* const* is
             const int bn = tc_pick_width(&g, 1, tc_sm_count());
             const int R = role == 1 ? tc::BM : bn;
             const int rows = role == 1 ? g.M : g.N;
-            const long long nf = tc_presplit_floats(rows, g.K, R);
+            const long long nf = tc_presplit_floats(rows, g.K, R, role == 2);
             for (int h = 0; h < 2; ++h) {
                 const float* Mat = h == 0 ? s.Wm[a] : s.Vm[a];
                 FDM_CUDA(cudaMallocAsync((void**)&s.pre[a][h], (size_t)nf * sizeof(float), st));
                 // x axis: A(x', k) = M[x' + k ld]; y/z axes: B(n, k) = M[n + k ld]
-                FDM_CUDA(launch_tc_presplit(Mat, 1, ld, rows, g.K, R, s.pre[a][h], st));
+                FDM_CUDA(launch_tc_presplit(Mat, 1, ld, rows, g.K, R, role == 2, s.pre[a][h], st));
             }
             s.pre_role[a] = role;
             s.pre_bn[a] = bn;
@@ -719,13 +719,13 @@ cudaError_t tc_gemm_entry(const TcGemmArgs& in, cudaStream_t st) {
         if (g.pre == 2 && g.bn == 0) g.bn = tc_pick_width(&g, 1, tc_sm_count());
         const int R = g.pre == 1 ? tc::BM : g.bn;
         const int rows = g.pre == 1 ? g.M : g.N;
-        e = cudaMallocAsync((void**)&tmp, (size_t)tc_presplit_floats(rows, g.K, R) * sizeof(float), st);
+        e = cudaMallocAsync((void**)&tmp, (size_t)tc_presplit_floats(rows, g.K, R, g.pre == 2) * sizeof(float), st);
         if (e != cudaSuccess) return e;
         if (g.pre == 1) {
-            e = launch_tc_presplit(g.A, g.sAm, g.sAk, rows, g.K, R, tmp, st);
+            e = launch_tc_presplit(g.A, g.sAm, g.sAk, rows, g.K, R, false, tmp, st);
             g.A = tmp;
         } else {
-            e = launch_tc_presplit(g.B, g.sBn, g.sBk, rows, g.K, R, tmp, st);
+            e = launch_tc_presplit(g.B, g.sBn, g.sBk, rows, g.K, R, true, tmp, st);
             g.B = tmp;
         }
     }

@@ -260,12 +260,21 @@ __global__ void __launch_bounds__(256) source_pw_rows_kernel(const SourceArgs a)
         ty[c] = (a.dim < 2) ? (c == 0 ? from_double<CT>(1.0) : zero_v<CT>())
                             : (c < cy ? tab<CT>(a.ax[1].TW, j * wy + c) : zero_v<CT>());
     }
+    // the products of the x and y test weights, once for all the thread's planes
+    CT txy[MAXW][MAXW];
+#pragma unroll
+    for (int by = 0; by < MAXW; ++by)
+#pragma unroll
+        for (int c = 0; c < MAXW; ++c) {
+            if constexpr (std::is_same<CT, double>::value) txy[by][c] = ty[by] * tx[c];
+            else txy[by][c] = df_mul(ty[by], tx[c]);
+        }
     for (int k = blockIdx.y; k < nz; k += gridDim.y) {
         const long long e = (long long)k * plane + pe;
         const int wz = a.dim >= 3 ? a.ax[2].wq : 1, psz = a.dim >= 3 ? a.ax[2].pstart[k] : 0;
         const int cz = a.dim >= 3 ? a.ax[2].pcount[k] : 1;
-        // b = sum_z tz (sum_y ty (sum_x tx f)): the x sums of the sample rows,
-        // weighted by ty into a y sum per z point, weighted by tz into b
+        // b = sum_z tz (sum_{y,x} (ty tx) f): per z point of the cell one
+        // compensated sum over its y-by-x samples, weighted by tz into b
         Acc<CT> acc;
         acc.init();
         for (int az = 0; az < cz; ++az) {
@@ -302,27 +311,20 @@ __global__ void __launch_bounds__(256) source_pw_rows_kernel(const SourceArgs a)
             }
             // every sum starts from its first product (the windows hold at
             // least one point unless the row is a Dirichlet row)
-            Acc<CT> sy;
-            sy.init();
+            Acc<CT> sxy;
+            if (cx > 0 && cy > 0) acc_first_prod_f(sxy, txy[0][0], fv[0][0]);
+            else sxy.init();
 #pragma unroll
-            for (int by = 0; by < MAXW; ++by) {
-                if (by < cy) {
-                    Acc<CT> sx;
-                    if (cx > 0) acc_first_prod_f(sx, tx[0], fv[by][0]);
-                    else sx.init();
+            for (int by = 0; by < MAXW; ++by)
 #pragma unroll
-                    for (int c = 1; c < MAXW; ++c) {
-                        if (c < cx) {
-                            if constexpr (std::is_same<CT, double>::value) sx.add_prod(tx[c], (double)fv[by][c]);
-                            else sx.add_prod_f(tx[c], (float)fv[by][c]);
-                        }
+                for (int c = 0; c < MAXW; ++c) {
+                    if ((by > 0 || c > 0) && by < cy && c < cx) {
+                        if constexpr (std::is_same<CT, double>::value) sxy.add_prod(txy[by][c], (double)fv[by][c]);
+                        else sxy.add_prod_f(txy[by][c], (float)fv[by][c]);
                     }
-                    if (by == 0) acc_first_prod(sy, ty[0], sx.result());
-                    else sy.add_prod(ty[by], sx.result());
                 }
-            }
-            if (az == 0) acc_first_prod(acc, tz, sy.result());
-            else acc.add_prod(tz, sy.result());
+            if (az == 0) acc_first_prod(acc, tz, sxy.result());
+            else acc.add_prod(tz, sxy.result());
         }
         const CT r = acc.result();
         if (!IGAPW_IDX("source rows out", e, a.ntot)) continue;

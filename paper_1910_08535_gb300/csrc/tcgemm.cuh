@@ -26,8 +26,9 @@
 //     copies (cp.async.bulk) that complete on a per-stage mbarrier, and the
 //     loaders handle the other operand only;
 //   - warp 8 waits until the stage is complete (the loaders' `full` barrier
-//     and the copy's), issues the chunk's 12 MMAs (4 K-steps x 3 products)
-//     and commits them to the stage's `empty` mbarrier, which the loaders and
+//     and the copy's), issues the chunk's 8 MMAs (4 K-steps, each
+//     A_hi [B_hi; B_lo] with N = 2 BN into adjacent accumulators and A_lo
+//     B_hi with N = BN) and commits them to the stage's `empty` mbarrier, which the loaders and
 //     warp 9 wait on before they refill the stage; the MMAs of a group of
 //     two chunks write fresh partial sums into one of two tensor-memory
 //     buffers;
@@ -99,11 +100,13 @@ __host__ __device__ constexpr unsigned tc_tile_offset(int rows, int r, int k) {
 // both live: no raw tile, the loaders read global memory themselves).
 template <int BN, int PRE>
 __host__ __device__ constexpr int tc_raw_rows() { return PRE == 1 ? BN : PRE == 2 ? tc::BM : 0; }
-// A stage: hi and lo tiles of A and B, then the live operand's raw FP32
-// chunk as TMA writes it (rows x 32 floats, or 32 x rows).
+// A stage: the hi and lo tiles of A, one tile of 2 BN rows holding B's hi
+// rows then its lo rows (so that one MMA with N = 2 BN takes A_hi B_hi and
+// A_hi B_lo together), then the live operand's raw FP32 chunk as TMA writes
+// it (rows x 32 floats, or 32 x rows).
 template <int BN, int PRE>
 __host__ __device__ constexpr unsigned tc_stage_bytes() {
-    return 2u * (tc_tile_bytes(tc::BM) + tc_tile_bytes(BN)) + (unsigned)tc_raw_rows<BN, PRE>() * tc::BK * 4u;
+    return 2u * tc_tile_bytes(tc::BM) + tc_tile_bytes(2 * BN) + (unsigned)tc_raw_rows<BN, PRE>() * tc::BK * 4u;
 }
 
 // Tensor-memory columns allocated for the accumulators of a BN-wide tile:
@@ -127,10 +130,17 @@ __host__ __device__ constexpr size_t tc_smem_bytes() {
     return (size_t)tc_stages<BN, PRE>() * tc_stage_bytes<BN, PRE>() + 256;
 }
 
+// Bytes of one block of a pre-split operand with tiles of R rows: the hi
+// tile then the lo tile (an A operand), or one tile of 2 R rows with the hi
+// rows first (a B operand, `comb`), the layouts of a stage.
+__host__ __device__ constexpr unsigned tc_presplit_block_bytes(int R, bool comb) {
+    return comb ? tc_tile_bytes(2 * R) : 2u * tc_tile_bytes(R);
+}
+
 // Floats of the pre-split form of a rows x K operand with tiles of R rows:
-// ceil(rows / R) x ceil(K / 32) blocks, each the hi tile then the lo tile.
-inline long long tc_presplit_floats(int rows, int K, int R) {
-    return (long long)((rows + R - 1) / R) * ((K + tc::BK - 1) / tc::BK) * 2 * (tc_tile_bytes(R) / 4);
+// ceil(rows / R) x ceil(K / 32) blocks.
+inline long long tc_presplit_floats(int rows, int K, int R, bool comb) {
+    return (long long)((rows + R - 1) / R) * ((K + tc::BK - 1) / tc::BK) * (tc_presplit_block_bytes(R, comb) / 4);
 }
 
 #ifndef IGAPW_HOST_EMU
@@ -165,8 +175,21 @@ __device__ __forceinline__ bool mbar_try(unsigned long long* bar, unsigned parit
     return done != 0;
 }
 
+// Non-blocking test of the phase (cheaper than a try_wait on a phase that
+// completed long ago)
+__device__ __forceinline__ bool mbar_test(unsigned long long* bar, unsigned parity) {
+    unsigned done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+
 // Bounded wait for the mbarrier phase `parity` to complete; false on timeout.
 __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity) {
+    if (mbar_test(bar, parity)) return true;
     for (unsigned it = 0; it < kSpinLimit; ++it)
         if (mbar_try(bar, parity)) return true;
     return false;
@@ -175,6 +198,7 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned pari
 // Bounded wait that also gives up when another warp has aborted; false on
 // timeout or abort (a timeout raises the abort flag).
 __device__ __forceinline__ bool mbar_wait_or_abort(unsigned long long* bar, unsigned parity, volatile int* abort_flag) {
+    if (mbar_test(bar, parity)) return true;
     for (unsigned it = 0; it < kSpinLimit; ++it) {
         if (mbar_try(bar, parity)) return true;
         if (*abort_flag) return false;
@@ -288,7 +312,9 @@ __device__ __forceinline__ int operand_mode(const float* src, long long sR, long
 // K): item j of a thread is warp item w = warp + 8 j (R / 32 items per
 // thread).  KVEC/SCALAR: row 4 w + lane / 8, K group lane % 8.  MVEC: rows
 // 32 (w % (R/32)) + 4 (lane % 8) .. + 3, K value 4 (w / (R/32)) + lane / 8.
-template <int R>
+// The shared tiles it writes have LR rows (R for A; 2 R for B, whose lo rows
+// follow its hi rows in the same tile).
+template <int R, int LR = R>
 struct Loader {
     static constexpr int N = R / 32;
     const float* src;
@@ -362,9 +388,9 @@ struct Loader {
                 // four rows, one K value: four scalar stores
                 const int r = 32 * (w % (R / 32)) + 4 * (lane & 7);
                 const int k = 4 * (w / (R / 32)) + (lane >> 3);
-                const unsigned o0 = tc_tile_offset(R, r, k);
-                const unsigned d1 = tc_tile_offset(R, r + 1, k) - o0, d2 = tc_tile_offset(R, r + 2, k) - o0,
-                               d3 = tc_tile_offset(R, r + 3, k) - o0;
+                const unsigned o0 = tc_tile_offset(LR, r, k);
+                const unsigned d1 = tc_tile_offset(LR, r + 1, k) - o0, d2 = tc_tile_offset(LR, r + 2, k) - o0,
+                               d3 = tc_tile_offset(LR, r + 3, k) - o0;
                 *reinterpret_cast<float*>(thi + o0) = h.x;
                 *reinterpret_cast<float*>(thi + o0 + d1) = h.y;
                 *reinterpret_cast<float*>(thi + o0 + d2) = h.z;
@@ -375,7 +401,7 @@ struct Loader {
                 *reinterpret_cast<float*>(tlo + o0 + d3) = l.w;
             } else {
                 const int r = 4 * w + (lane >> 3);
-                const unsigned off = tc_tile_offset(R, r, 4 * (lane & 7));
+                const unsigned off = tc_tile_offset(LR, r, 4 * (lane & 7));
                 *reinterpret_cast<float4*>(thi + off) = h;
                 *reinterpret_cast<float4*>(tlo + off) = l;
             }
@@ -393,10 +419,11 @@ __device__ __forceinline__ void tc_tile(const TcGemmArgs& g, const int m0, const
     using namespace tc;
     constexpr int NS = tc_stages<BN, PRE>();
     constexpr unsigned STAGE = tc_stage_bytes<BN, PRE>();
-    constexpr unsigned RAW = 2u * (tc_tile_bytes(BM) + tc_tile_bytes(BN));   // raw tile offset in a stage
+    constexpr unsigned RAW = 2u * tc_tile_bytes(BM) + tc_tile_bytes(2 * BN);   // raw tile offset in a stage
     constexpr int RR = tc_raw_rows<BN, PRE>();
-    constexpr unsigned TA = tc_tile_bytes(BM), TB = tc_tile_bytes(BN);
-    constexpr unsigned LBOA = tc_lbo(BM), LBOB = tc_lbo(BN);
+    constexpr unsigned TA = tc_tile_bytes(BM), TB2 = tc_tile_bytes(2 * BN);
+    constexpr unsigned LBOA = tc_lbo(BM), LBOB2 = tc_lbo(2 * BN);
+    constexpr unsigned BLO = (unsigned)(BN / 8) * kTcSbo;   // B's lo rows after its hi rows
     static_assert(NS >= 2 && (3 * NS + 5) * 8 + 8 <= 256, "stage count");
     extern __shared__ __align__(1024) unsigned char tsm_raw[];
     unsigned long long* full = reinterpret_cast<unsigned long long*>(tsm_raw + NS * STAGE);
@@ -442,7 +469,7 @@ __device__ __forceinline__ void tc_tile(const TcGemmArgs& g, const int m0, const
         const float* A = g.A + (long long)b * g.bA;
         const float* Bm = g.B + (long long)b * g.bB;
         const Loader<BM> la{A, g.sAm, g.sAk, operand_mode(A, g.sAm, g.sAk), g.M, m0, g.K, warp, lane};
-        const Loader<BN> lb{Bm, g.sBn, g.sBk, operand_mode(Bm, g.sBn, g.sBk), g.N, n0, g.K, warp, lane};
+        const Loader<BN, 2 * BN> lb{Bm, g.sBn, g.sBk, operand_mode(Bm, g.sBn, g.sBk), g.N, n0, g.K, warp, lane};
         // The live operands of the next PD chunks wait in registers (PD sets
         // used in turn); a chunk's loads are issued after the previous
         // chunk's stores are fenced and published, so the fence never waits
@@ -526,7 +553,7 @@ __device__ __forceinline__ void tc_tile(const TcGemmArgs& g, const int m0, const
                 return;
             }
             if (PRE != 1) la.store(xa, st, st + TA);
-            if (PRE != 2) lb.store(xb, st + 2 * TA, st + 2 * TA + TB);
+            if (PRE != 2) lb.store(xb, st + 2 * TA, st + 2 * TA + BLO);
             // generic-proxy stores -> visible to the tensor core (async proxy)
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             mbar_arrive(&full[s]);
@@ -565,7 +592,7 @@ __device__ __forceinline__ void tc_tile(const TcGemmArgs& g, const int m0, const
         }
     } else if (warp == kLoadWarps) {
         // ---- MMA warp: lane 0 issues, the warp follows --------------------------
-        const unsigned idesc = instr_desc<BN>();
+        const unsigned idesc = instr_desc<BN>(), idesc2 = instr_desc<2 * BN>();
         for (int c = 0; c < nchunks; ++c) {
             const int s = c % NS, q = c / kGroup, buf = q & 1;
             const bool first = c % kGroup == 0, last = c % kGroup == kGroup - 1 || c == nchunks - 1;
@@ -587,12 +614,13 @@ __device__ __forceinline__ void tc_tile(const TcGemmArgs& g, const int m0, const
                     // K = 8 step ks: core-matrix columns 2 ks, 2 ks + 1
                     const unsigned long long dah = smem_desc(st + 2 * ks * LBOA, LBOA, kTcSbo);
                     const unsigned long long dal = smem_desc(st + TA + 2 * ks * LBOA, LBOA, kTcSbo);
-                    const unsigned long long dbh = smem_desc(st + 2 * TA + 2 * ks * LBOB, LBOB, kTcSbo);
-                    const unsigned long long dbl = smem_desc(st + 2 * TA + TB + 2 * ks * LBOB, LBOB, kTcSbo);
+                    const unsigned long long db = smem_desc(st + 2 * TA + 2 * ks * LBOB2, LBOB2, kTcSbo);
                     const unsigned acc = (first && ks == 0) ? 0u : 1u;
-                    mma_tf32(dhh, dah, dbh, idesc, acc);
-                    mma_tf32(dx, dah, dbl, idesc, acc);
-                    mma_tf32(dx, dal, dbh, idesc, 1u);
+                    // A_hi [B_hi; B_lo] into the adjacent (hi x hi, cross)
+                    // accumulators with N = 2 BN, then A_lo B_hi (the first BN
+                    // rows of the B tile) into the cross one
+                    mma_tf32(dhh, dah, db, idesc2, acc);
+                    mma_tf32(dx, dal, db, idesc, 1u);
                 }
                 mma_commit(&empty[s]);
                 if (last) mma_commit(&accf[buf]);
@@ -609,10 +637,10 @@ __device__ __forceinline__ void tc_tile(const TcGemmArgs& g, const int m0, const
     } else if (PRE != 0 && lane == 0) {
         // ---- bulk-copy thread: the pre-split operand's chunks -------------------
         const int rt = PRE == 1 ? m0 / BM : n0 / BN;
-        const unsigned tb = PRE == 1 ? TA : TB;
+        const unsigned blk = PRE == 1 ? 2u * TA : TB2;   // bytes of one pre-split block
         const long long bstride = PRE == 1 ? g.bA : g.bB;
         const float* base = (PRE == 1 ? g.A : g.B) + (long long)b * bstride +
-                            (long long)rt * nchunks * 2 * (tb / 4);
+                            (long long)rt * nchunks * (blk / 4);
         unsigned char* dst0 = tsm_raw + (PRE == 1 ? 0u : 2u * TA);
         // the live operand's raw chunk by TMA: rows r0.. of the live operand,
         // coordinates (k, row, batch) or (row, k, batch) after its unit stride
@@ -626,8 +654,8 @@ __device__ __forceinline__ void tc_tile(const TcGemmArgs& g, const int m0, const
         for (int c = 0; c < nchunks; ++c) {
             const int s = c % NS;
             if (c >= NS && !mbar_wait_or_abort(&empty[s], (unsigned)((c / NS) - 1) & 1u, abort_flag)) break;
-            mbar_arrive_expect_tx(&txb[s], 2u * tb + (tma ? RAWB : 0u));
-            bulk_copy(dst0 + s * STAGE, base + (long long)c * 2 * (tb / 4), 2u * tb, &txb[s]);
+            mbar_arrive_expect_tx(&txb[s], blk + (tma ? RAWB : 0u));
+            bulk_copy(dst0 + s * STAGE, base + (long long)c * (blk / 4), blk, &txb[s]);
             if (tma) {
                 unsigned char* rdst = tsm_raw + s * STAGE + RAW;
                 if (lmode == MVEC) tma_load3(rdst, g.tmap, lr0, c * BK, lz, &txb[s]);
@@ -665,10 +693,12 @@ __global__ void __launch_bounds__(tc::kThreads, 1) tc_gemm_grouped_kernel(const 
 
 // Pre-split form of a rows x K operand X(r, k) = X[r * sR + k * sK] with
 // tiles of R rows (tc_presplit_floats floats at `out`; zero outside X and in
-// the layout's gaps).
-static __global__ void tc_presplit_kernel(const float* X, long long sR, long long sK, int rows, int K, int R, float* out) {
+// the layout's gaps): per block the hi tile then the lo tile (A), or one tile
+// of 2 R rows, hi rows first (B, `comb`).
+static __global__ void tc_presplit_kernel(const float* X, long long sR, long long sK, int rows, int K, int R, bool comb,
+                                          float* out) {
     const int nkc = (K + tc::BK - 1) / tc::BK;
-    const long long per_block = 2 * (long long)(tc_tile_bytes(R) / 4);
+    const long long per_block = (long long)(tc_presplit_block_bytes(R, comb) / 4);
     const long long total = (long long)((rows + R - 1) / R) * nkc * R * tc::BK;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
          i += (long long)gridDim.x * blockDim.x) {
@@ -682,20 +712,25 @@ static __global__ void tc_presplit_kernel(const float* X, long long sR, long lon
         float hi, lo;
         tc::split_tf32(x, hi, lo);
         float* dst = out + blk * per_block;
-        const unsigned o = tc_tile_offset(R, rr, kk) / 4;
-        dst[o] = hi;
-        dst[tc_tile_bytes(R) / 4 + o] = lo;
+        if (comb) {
+            dst[tc_tile_offset(2 * R, rr, kk) / 4] = hi;
+            dst[tc_tile_offset(2 * R, R + rr, kk) / 4] = lo;
+        } else {
+            const unsigned o = tc_tile_offset(R, rr, kk) / 4;
+            dst[o] = hi;
+            dst[tc_tile_bytes(R) / 4 + o] = lo;
+        }
     }
 }
 
-inline cudaError_t launch_tc_presplit(const float* X, long long sR, long long sK, int rows, int K, int R, float* out,
-                                      cudaStream_t st) {
+inline cudaError_t launch_tc_presplit(const float* X, long long sR, long long sK, int rows, int K, int R, bool comb,
+                                      float* out, cudaStream_t st) {
     if (rows <= 0 || K <= 0 || (R % 32) != 0) return cudaErrorInvalidValue;
-    cudaError_t e = cudaMemsetAsync(out, 0, (size_t)tc_presplit_floats(rows, K, R) * sizeof(float), st);
+    cudaError_t e = cudaMemsetAsync(out, 0, (size_t)tc_presplit_floats(rows, K, R, comb) * sizeof(float), st);
     if (e != cudaSuccess) return e;
     const long long total = (long long)((rows + R - 1) / R) * ((K + tc::BK - 1) / tc::BK) * R * tc::BK;
     const unsigned grid = (unsigned)std::min<long long>((total + 255) / 256, 4096);
-    tc_presplit_kernel<<<grid, 256, 0, st>>>(X, sR, sK, rows, K, R, out);
+    tc_presplit_kernel<<<grid, 256, 0, st>>>(X, sR, sK, rows, K, R, comb, out);
     return cudaGetLastError();
 }
 
@@ -751,11 +786,12 @@ constexpr int kTcWidths[3] = {64, 96, 128};
 // Estimated time (arbitrary units) of tiles of width bn over `sms` SMs: the
 // split-TF32 MMAs with N <= 256 are bound by shared-memory bandwidth (about
 // 128 bytes per clock on an SM), so a K chunk of one tile costs its shared
-// traffic: the 12 MMAs read A (BM x 8) and B (bn x 8) 4-byte values each,
-// and the hi and lo parts of both operands are written once.  Tiles are
+// traffic: per K step the two MMAs read A_hi and A_lo (BM x 8 each) and B
+// (2 bn x 8 and bn x 8) 4-byte values, and the hi and lo parts of both
+// operands are written once.  Tiles are
 // spread over the SMs, so the busiest SM holds ceil(tiles / sms) of them.
 inline double tc_cost(long long tiles, int bn, long long chunks, int sms) {
-    const double per_chunk = (12.0 * (tc::BM + bn) * 8 * 4 + 2.0 * (tc::BM + bn) * tc::BK * 4) / 128.0;
+    const double per_chunk = (4.0 * (2 * tc::BM + 3 * bn) * 8 * 4 + 2.0 * (tc::BM + bn) * tc::BK * 4) / 128.0;
     return (double)((tiles + sms - 1) / sms) * per_chunk * (double)chunks;
 }
 
