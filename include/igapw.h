@@ -335,13 +335,19 @@ int igapw_destroy(igapw_ctx* ctx);
  * into shared-memory tiles before the product and streamed by bulk copies,
  * the path the solver takes for its constant matrices; a pre-split operand
  * must have batch stride 0 when batch > 1.  bn: tile width (0, 64, 96 or
- * 128; 0 lets the cost model choose).  Synchronous on cuda_stream (NULL:
- * the legacy default stream).  IGAPW_ERR_TIMEOUT if a pipeline wait of the
- * kernel timed out; the message is in igapw_last_error(NULL).  Allocates a
- * temporary buffer when pre != 0. */
+ * 128; 0 lets the cost model choose).  splits: K split over several CTAs
+ * per tile when the tiles alone leave SMs idle (0: the cost model chooses
+ * the split together with the width; 1: none; 2-4: that many equal ranges of
+ * 32-wide K chunks, at most ceil(K / 32)); each CTA writes its FP32 partial
+ * tile to a workspace and the tile's last CTA adds the partials in a fixed
+ * order, so the result does not depend on the CTAs' timing.  Synchronous on
+ * cuda_stream (NULL: the legacy default stream).  IGAPW_ERR_TIMEOUT if a
+ * pipeline wait of the kernel timed out; the message is in
+ * igapw_last_error(NULL).  Allocates temporary buffers when pre != 0 or K
+ * is split. */
 int igapw_tc_gemm(int M, int N, int K, int batch, const float* A, long long sAm, long long sAk, long long bA,
                   const float* B, long long sBn, long long sBk, long long bB, float* D, long long sDm, long long sDn,
-                  long long bD, int pre, int bn, void* cuda_stream);
+                  long long bD, int pre, int bn, int splits, void* cuda_stream);
 
 /* ---- batched 2D Poisson over many uneven instances ----------------------
  * The problem of Sec. 4.3 (-Lap u = f, zero Dirichlet rows, Eq. (7) tested

@@ -402,11 +402,13 @@ int enqueue_steps(igapw_ctx* c, double dt, int nsteps, void* u, cudaStream_t st)
 
 // Split-step autotuner: per axis, times every launch shape of the step kernels
 // (chunked with 32 / 16 / 8 lines; staged tables with 32 / 16 / 8 lines or
-// columns; tables in global memory with 32 / 16 / 8) on zeroed scratch tensors
+// columns; tables in global memory with 32 down to 1, the narrow shapes for
+// lines of several thousand rows) on zeroed scratch tensors
 // and keeps the first valid shape unless a later one is 10% faster.  Runs once
 // per context, before the first step is captured.
 int tune_step(igapw_ctx* c, double dt) {
-    static const int cand[][2] = {{3, 32}, {3, 16}, {3, 8}, {0, 32}, {0, 16}, {0, 8}, {2, 16}, {1, 32}, {1, 16}, {1, 8}};
+    static const int cand[][2] = {{3, 32}, {3, 16}, {3, 8}, {0, 32}, {0, 16}, {0, 8}, {2, 16},
+                                  {1, 32}, {1, 16}, {1, 8}, {1, 4}, {1, 2}, {1, 1}};
     const size_t bytes = (size_t)c->ntot * 8;   // one pair or FP64 tensor
     unsigned char *tu = nullptr, *tacc = nullptr;
     CKC(c, cudaMallocAsync((void**)&tu, bytes, c->stream));
@@ -981,12 +983,13 @@ int igapw_sync_status(igapw_ctx* c) {
 
 int igapw_tc_gemm(int M, int N, int K, int batch, const float* A, long long sAm, long long sAk, long long bA,
                   const float* B, long long sBn, long long sBk, long long bB, float* D, long long sDm, long long sDn,
-                  long long bD, int pre, int bn, void* cuda_stream) {
+                  long long bD, int pre, int bn, int splits, void* cuda_stream) {
     g_create_error.clear();
     if (M <= 0 || N <= 0 || K <= 0 || batch <= 0 || !A || !B || !D || pre < 0 || pre > 2 ||
-        (bn != 0 && bn != 64 && bn != 96 && bn != 128)) {
+        (bn != 0 && bn != 64 && bn != 96 && bn != 128) || splits < 0 || splits > kTcMaxSplits ||
+        splits > (K + 31) / 32 || (long long)batch * (splits > 1 ? splits : 1) > 65535) {
         g_create_error = "igapw_tc_gemm: need M, N, K, batch >= 1, non-NULL A, B, D, pre in {0, 1, 2}, bn in {0, 64, 96, "
-                         "128}";
+                         "128}, splits in 0 .. min(4, ceil(K / 32)), batch x splits <= 65535";
         return IGAPW_ERR_ARG;
     }
     if (pre != 0 && batch != 1 && (pre == 1 ? bA : bB) != 0) {
@@ -1000,6 +1003,7 @@ int igapw_tc_gemm(int M, int N, int K, int batch, const float* A, long long sAm,
     g.D = D; g.sDm = sDm; g.sDn = sDn; g.bD = bD;
     g.pre = pre;
     g.bn = bn;
+    g.splits = splits;
     const cudaError_t e = tc_gemm_entry(g, (cudaStream_t)cuda_stream);
     if (e == cudaErrorLaunchTimeout) {
         g_create_error = "igapw_tc_gemm: a pipeline wait of the kernel timed out";

@@ -465,6 +465,13 @@ static TcGemmArgs tc_axis_args(const FdmState& s, int a, const float* M, const f
         g.D = out; g.sDn = (long long)px * ny;
         if (pre) { g.B = pre; g.pre = 2; g.bn = s.pre_bn[a]; }
     }
+    // the planned split of K (its workspace and counters are the state's)
+    if (pre && s.splits[a] > 1) {
+        g.splits = s.splits[a];
+        for (int i = 0; i < 5; ++i) g.kb[i] = s.kb[a][i];
+        g.ws = s.tc_ws;
+        g.cnt = s.tc_cnt;
+    }
     // the live operand's tensor map, when one was made for this input buffer
     if (pre && s.tmaps) {
         const int buf = in == s.t[0] ? 0 : in == s.t[1] ? 1 : -1;
@@ -489,6 +496,11 @@ void fdm_release(FdmState& s) {
     }
     if (s.tmaps) cudaFreeAsync(s.tmaps, s.stream);
     s.tmaps = nullptr;
+    if (s.tc_ws) cudaFreeAsync(s.tc_ws, s.stream);
+    if (s.tc_cnt) cudaFreeAsync(s.tc_cnt, s.stream);
+    s.tc_ws = nullptr;
+    s.tc_cnt = nullptr;
+    for (int a = 0; a < 3; ++a) s.splits[a] = 1;
     if (s.blas) cublasDestroy(s.blas);
     s.blas = nullptr;
     for (int a = 0; a < 3; ++a) {
@@ -541,12 +553,19 @@ int fdm_build(FdmState& s, int dim, const FdmAxisInput* ax, const int* const* is
     if (S) FDM_CUDA(cudaStreamSynchronize(S->ss));
     FDM_BLAS(cublasSetStream(s.blas, st));
     if (gemm == FDM_GEMM_TC) {
-        // the constant operand of every transform, split once (gemm_axis)
+        // the constant operand of every transform, split once (gemm_axis),
+        // for the planned tile width; the split of K and its workspace
+        long long ws_floats = 0, counters = 0;
         for (int a = 0; a < dim; ++a) {
             TcGemmArgs g = tc_axis_args(s, a, nullptr, nullptr, nullptr, nullptr);
             const int ld = s.axis[a]->np;
             const int role = a == 0 ? 1 : 2;
-            const int bn = tc_pick_width(&g, 1, tc_sm_count());
+            const TcPlan plan = tc_plan(g, tc_sm_count(), 0, true);
+            const int bn = plan.bn;
+            s.splits[a] = plan.splits;
+            for (int i = 0; i < 5; ++i) s.kb[a][i] = plan.kb[i];
+            ws_floats = std::max(ws_floats, tc_split_ws_floats(g, plan));
+            counters = std::max(counters, tc_split_counters(g, plan));
             const int R = role == 1 ? tc::BM : bn;
             const int rows = role == 1 ? g.M : g.N;
             const long long nf = tc_presplit_floats(rows, g.K, R, role == 2);
@@ -558,6 +577,11 @@ int fdm_build(FdmState& s, int dim, const FdmAxisInput* ax, const int* const* is
             }
             s.pre_role[a] = role;
             s.pre_bn[a] = bn;
+        }
+        if (ws_floats > 0) {
+            FDM_CUDA(cudaMallocAsync((void**)&s.tc_ws, (size_t)ws_floats * sizeof(float), st));
+            FDM_CUDA(cudaMallocAsync((void**)&s.tc_cnt, (size_t)counters * sizeof(unsigned), st));
+            FDM_CUDA(cudaMemsetAsync(s.tc_cnt, 0, (size_t)counters * sizeof(unsigned), st));
         }
         // tensor maps of the spectral operand for TMA loads: the live operand
         // is B (x axis, tiles of bn rows) or A (y/z axes, tiles of 128 rows),
@@ -701,27 +725,50 @@ int fdm_solve(FdmState& s, const ContractArgs& ca, const void* b, void* u, bool 
 
 // The tensor-core GEMM on caller buffers (igapw_tc_gemm): synchronous; a
 // pre-split operand (pre = 1: A, 2: B) is split into a temporary buffer
-// first.  Returns a CUDA error, or cudaErrorLaunchTimeout when a pipeline
-// wait of the kernel timed out.
+// first.  in.splits: 0 = tile width and split of K from tc_plan, 1 = no
+// split, 2-4 = that many equal chunk ranges (temporary workspace and
+// counters).  Returns a CUDA error, or cudaErrorLaunchTimeout when a
+// pipeline wait of the kernel timed out.
 static __device__ unsigned g_tc_entry_status;
 
 cudaError_t tc_gemm_entry(const TcGemmArgs& in, cudaStream_t st) {
     TcGemmArgs g = in;
+    if ((g.pre == 1 || g.pre == 2) && g.batch != 1 && (g.pre == 1 ? g.bA : g.bB) != 0) return cudaErrorInvalidValue;
+    const int sms = tc_sm_count();
+    const int nkc = (g.K + tc::BK - 1) / tc::BK;
+    TcPlan plan;
+    if (g.splits == 0) {
+        plan = tc_plan(g, sms, g.bn, true);
+    } else {
+        if (g.splits < 0 || g.splits > kTcMaxSplits || g.splits > nkc) return cudaErrorInvalidValue;
+        plan.bn = g.bn ? g.bn : tc_pick_width(&g, 1, sms);
+        plan.splits = g.splits;
+        for (int i = 0; i < 5; ++i) plan.kb[i] = i <= plan.splits ? (int)((long long)nkc * i / plan.splits) : nkc;
+    }
     unsigned* status = nullptr;
     cudaError_t e = cudaGetSymbolAddress((void**)&status, g_tc_entry_status);
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(status, 0, sizeof(unsigned), st);
     if (e != cudaSuccess) return e;
     g.status = status;
+    float* ws = nullptr;
+    unsigned* cnt = nullptr;
+    if (plan.splits > 1) {
+        e = cudaMallocAsync((void**)&ws, (size_t)tc_split_ws_floats(g, plan) * sizeof(float), st);
+        if (e == cudaSuccess)
+            e = cudaMallocAsync((void**)&cnt, (size_t)tc_split_counters(g, plan) * sizeof(unsigned), st);
+        if (e == cudaSuccess)
+            e = cudaMemsetAsync(cnt, 0, (size_t)tc_split_counters(g, plan) * sizeof(unsigned), st);
+    }
+    tc_apply_plan(g, plan, ws, cnt);
     float* tmp = nullptr;
-    if (g.pre == 1 || g.pre == 2) {
-        if (g.batch != 1 && (g.pre == 1 ? g.bA : g.bB) != 0) return cudaErrorInvalidValue;
-        if (g.pre == 2 && g.bn == 0) g.bn = tc_pick_width(&g, 1, tc_sm_count());
+    if (e == cudaSuccess && (g.pre == 1 || g.pre == 2)) {
         const int R = g.pre == 1 ? tc::BM : g.bn;
         const int rows = g.pre == 1 ? g.M : g.N;
         e = cudaMallocAsync((void**)&tmp, (size_t)tc_presplit_floats(rows, g.K, R, g.pre == 2) * sizeof(float), st);
-        if (e != cudaSuccess) return e;
-        if (g.pre == 1) {
+        if (e != cudaSuccess) {
+            tmp = nullptr;
+        } else if (g.pre == 1) {
             e = launch_tc_presplit(g.A, g.sAm, g.sAk, rows, g.K, R, false, tmp, st);
             g.A = tmp;
         } else {
@@ -732,7 +779,6 @@ cudaError_t tc_gemm_entry(const TcGemmArgs& in, cudaStream_t st) {
     // the live operand by TMA where a tensor map can describe it
     void* dmap = nullptr;
     if (e == cudaSuccess && (g.pre == 1 || g.pre == 2)) {
-        if (g.pre == 1 && g.bn == 0) g.bn = tc_pick_width(&g, 1, tc_sm_count());
         CUtensorMap hm;
         const int R = g.pre == 1 ? g.bn : tc::BM;
         const bool ok = g.pre == 1 ? tc_make_tmap(&hm, g.B, g.sBn, g.sBk, g.bB, g.N, g.K, g.batch, R)
@@ -747,6 +793,8 @@ cudaError_t tc_gemm_entry(const TcGemmArgs& in, cudaStream_t st) {
     if (e == cudaSuccess) e = launch_tc_gemm(g, st);
     if (tmp) cudaFreeAsync(tmp, st);
     if (dmap) cudaFreeAsync(dmap, st);
+    if (ws) cudaFreeAsync(ws, st);
+    if (cnt) cudaFreeAsync(cnt, st);
     const cudaError_t e2 = cudaStreamSynchronize(st);
     if (e == cudaSuccess) e = e2;
     if (e != cudaSuccess) return e;

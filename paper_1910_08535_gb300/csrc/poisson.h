@@ -61,6 +61,13 @@ struct FdmState {
     void* tmaps = nullptr;
     bool tmap_ok[3][2] = {{false, false}, {false, false}, {false, false}};
     int tmap_rows[3] = {0, 0, 0};
+    // split of K per axis (tcgemm.cuh's tc_plan: splits, chunk boundaries;
+    // the tile width is pre_bn), the split products' partial tiles and
+    // per-tile counters (zero between launches)
+    int splits[3] = {1, 1, 1};
+    int kb[3][5] = {};
+    float* tc_ws = nullptr;
+    unsigned* tc_cnt = nullptr;
 };
 
 // Engines of the dense per-axis transforms: the library's tcgen05 split-TF32

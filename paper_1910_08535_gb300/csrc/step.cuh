@@ -132,8 +132,9 @@ __global__ void __launch_bounds__(256) axis_step_kernel(const AxisStepArgs a) {
     // lines carry W zero rows past n, so the contraction windows need no guards
     const int nr = n + W;
     // staged y/z blocks always hold 32 columns: a compile-time pitch of 33 turns
-    // the row offsets of the banded windows into immediate offsets
-    const int pitch = XL ? (nr | 1) : (TG ? NL + 1 : (CFG == 2 ? 17 : 33));
+    // the row offsets of the banded windows into immediate offsets; a single
+    // column (lines too long for more) needs no padding against bank conflicts
+    const int pitch = XL ? (nr | 1) : (TG ? (NL == 1 ? 1 : NL + 1) : (CFG == 2 ? 17 : 33));
     const int st = XL ? 1 : pitch;      // row stride within a line
     const int lst = XL ? pitch : 1;     // line stride
     const int cap = XL ? NL * pitch : nr * pitch;
@@ -357,7 +358,7 @@ static cudaError_t run_axis_step(const AxisStepArgs& a0, cudaStream_t st) {
     // bytes of shared memory for nl lines (XL) or nl columns, with or without
     // the tables staged
     auto smem_for = [&](int nl, bool tg) {
-        const size_t cap = xl ? (size_t)nl * ((n + W) | 1) : (size_t)(n + W) * (nl + 1);
+        const size_t cap = xl ? (size_t)nl * ((n + W) | 1) : (size_t)(n + W) * (tg && nl == 1 ? 1 : nl + 1);
         size_t b = (size_t)2 * cap * sizeof(VT);
         if (!tg)
             b += align16(table_elems<TS, KP>(n, a.ax.ls64.P) * sizeof(TS)) + align16((size_t)2 * n * W * sizeof(VT)) +

@@ -45,6 +45,8 @@
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <functional>
+#include <queue>
 #include <vector>
 
 #include "common.cuh"
@@ -74,7 +76,20 @@ struct TcGemmArgs {
     // for a live B, 128 for a live A).  Null: per-thread loads.
     const CUtensorMap* tmap;
     int tmap_rows;
+    // Split of K over several CTAs per tile (splits <= 1: none; at most
+    // kTcMaxSplits; single launches only, not grouped ones).  CTA z =
+    // s * batch + b sums the K chunks kb[s] .. kb[s+1]-1 (kb[0] = 0,
+    // kb[splits] = ceil(K / 32), every range non-empty) of tile (m, n, b) and
+    // writes the FP32 partial tile to ws (splits x tiles x 128 x bn floats);
+    // the last of the tile's CTAs to finish (counted in cnt[tile], zero before
+    // the launch and again after it) adds the partials in split order, so the
+    // result does not depend on which CTA finishes last, and stores D.
+    int splits;
+    int kb[5];
+    float* ws;
+    unsigned* cnt;
 };
+constexpr int kTcMaxSplits = 4;
 
 namespace tc {
 constexpr int BM = 128;
@@ -411,11 +426,12 @@ struct Loader {
 
 }  // namespace tc
 
-// One BM x BN tile of D (rows m0.., columns n0.., batch entry b) by one CTA
-// of 320 threads (roles in the header comment).  PRE = 0: both operands
-// live; 1: A pre-split; 2: B pre-split.
-template <int BN, int PRE>
-__device__ __forceinline__ void tc_tile(const TcGemmArgs& g, const int m0, const int n0, const int b) {
+// One BM x BN tile of D (rows m0.., columns n0.., batch entry b; the K
+// chunks of split sp when K is split) by one CTA of 320 threads (roles in the
+// header comment).  PRE = 0: both operands live; 1: A pre-split; 2: B
+// pre-split.  SPLIT = false compiles the split of K out (grouped launches).
+template <int BN, int PRE, bool SPLIT>
+__device__ __forceinline__ void tc_tile(const TcGemmArgs& g, const int m0, const int n0, const int b, const int sp) {
     using namespace tc;
     constexpr int NS = tc_stages<BN, PRE>();
     constexpr unsigned STAGE = tc_stage_bytes<BN, PRE>();
@@ -424,7 +440,7 @@ __device__ __forceinline__ void tc_tile(const TcGemmArgs& g, const int m0, const
     constexpr unsigned TA = tc_tile_bytes(BM), TB2 = tc_tile_bytes(2 * BN);
     constexpr unsigned LBOA = tc_lbo(BM), LBOB2 = tc_lbo(2 * BN);
     constexpr unsigned BLO = (unsigned)(BN / 8) * kTcSbo;   // B's lo rows after its hi rows
-    static_assert(NS >= 2 && (3 * NS + 5) * 8 + 8 <= 256, "stage count");
+    static_assert(NS >= 2 && (3 * NS + 5) * 8 + 12 <= 256, "stage count");
     extern __shared__ __align__(1024) unsigned char tsm_raw[];
     unsigned long long* full = reinterpret_cast<unsigned long long*>(tsm_raw + NS * STAGE);
     unsigned long long* empty = full + NS;
@@ -434,8 +450,12 @@ __device__ __forceinline__ void tc_tile(const TcGemmArgs& g, const int m0, const
     unsigned long long* done = acce + 2;
     unsigned* tmem_slot = reinterpret_cast<unsigned*>(done + 1);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+    volatile int* last_flag = abort_flag + 1;   // this CTA adds up the tile's partials
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int nchunks = (g.K + BK - 1) / BK;
+    const int nkc = (g.K + BK - 1) / BK;        // K chunks of the whole product
+    const bool split = SPLIT && g.splits > 1;
+    const int kc0 = split ? g.kb[sp] : 0;       // this CTA's chunks: kc0 .. kc0 + nchunks - 1
+    const int nchunks = split ? g.kb[sp + 1] - kc0 : nkc;
 
     if (tid == 0) {
         for (int i = 0; i < NS; ++i) {
@@ -481,8 +501,8 @@ __device__ __forceinline__ void tc_tile(const TcGemmArgs& g, const int m0, const
 #pragma unroll
         for (int j = 0; j < PD; ++j)
             if (j < nchunks && !tma) {
-                if (PRE != 1) la.fetch(j * BK, ra[j]);
-                if (PRE != 2) lb.fetch(j * BK, rb[j]);
+                if (PRE != 1) la.fetch((kc0 + j) * BK, ra[j]);
+                if (PRE != 2) lb.fetch((kc0 + j) * BK, rb[j]);
             }
         // Accumulation: the MMAs of a group of kGroup K chunks write fresh
         // partial sums into tensor-memory buffer (group % 2) (hi x hi products
@@ -558,8 +578,8 @@ __device__ __forceinline__ void tc_tile(const TcGemmArgs& g, const int m0, const
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             mbar_arrive(&full[s]);
             if (!tma && c + PD < nchunks) {
-                if (PRE != 1) la.fetch((c + PD) * BK, xa);
-                if (PRE != 2) lb.fetch((c + PD) * BK, xb);
+                if (PRE != 1) la.fetch((kc0 + c + PD) * BK, xa);
+                if (PRE != 2) lb.fetch((kc0 + c + PD) * BK, xb);
             }
             // the group before last, at the end of a group: its MMAs finished
             // a whole group ago, and its buffer is free again before the next
@@ -579,7 +599,44 @@ __device__ __forceinline__ void tc_tile(const TcGemmArgs& g, const int m0, const
 
         // ---- epilogue: warp w holds rows 32 (w % 4) + lane of the tile and
         // the column half w / 4
-        if (ok) {
+        bool store = ok;
+        if (split) {
+            // this split's partial tile, column-major (a warp writes 128
+            // contiguous bytes per column), then the CTA is counted in; the
+            // last of the tile's CTAs adds the partials in split order
+            const int mtc = (g.M + BM - 1) / BM, ntc = (g.N + BN - 1) / BN;
+            const long long tiles = (long long)mtc * ntc * g.batch;
+            const long long tile = ((long long)b * mtc + m0 / BM) * ntc + n0 / BN;
+            const long long tsz = (long long)BM * BN;
+            float* w0 = g.ws + tile * tsz + lq * 32 + lane + half * HC * BM;
+            float* wp = w0 + (long long)sp * tiles * tsz;
+#pragma unroll
+            for (int j = 0; j < HC; ++j) wp[j * BM] = acc[j];
+            __threadfence();
+            asm volatile("bar.sync 1, 256;" ::: "memory");   // the loader warps
+            if (tid == 0) {
+                __threadfence();
+                const unsigned prev = atomicAdd(g.cnt + tile, 1u);
+                const int last = prev == (unsigned)(g.splits - 1);
+                if (last) g.cnt[tile] = 0u;   // all splits counted: zero for the next launch
+                __threadfence();
+                *last_flag = last;
+            }
+            asm volatile("bar.sync 1, 256;" ::: "memory");
+            store = ok && *last_flag;
+            if (store) {
+                // every partial from the workspace (this CTA's own included),
+                // bypassing L1, in split order
+#pragma unroll
+                for (int j = 0; j < HC; ++j) acc[j] = __ldcg(w0 + j * BM);
+                for (int t = 1; t < g.splits; ++t) {
+                    const float* wt = w0 + (long long)t * tiles * tsz;
+#pragma unroll
+                    for (int j = 0; j < HC; ++j) acc[j] += __ldcg(wt + j * BM);
+                }
+            }
+        }
+        if (store) {
             const int row = m0 + lq * 32 + lane;
             float* Dp = g.D + (long long)b * g.bD;
             if (row < g.M) {
@@ -640,7 +697,7 @@ __device__ __forceinline__ void tc_tile(const TcGemmArgs& g, const int m0, const
         const unsigned blk = PRE == 1 ? 2u * TA : TB2;   // bytes of one pre-split block
         const long long bstride = PRE == 1 ? g.bA : g.bB;
         const float* base = (PRE == 1 ? g.A : g.B) + (long long)b * bstride +
-                            (long long)rt * nchunks * (blk / 4);
+                            ((long long)rt * nkc + kc0) * (blk / 4);
         unsigned char* dst0 = tsm_raw + (PRE == 1 ? 0u : 2u * TA);
         // the live operand's raw chunk by TMA: rows r0.. of the live operand,
         // coordinates (k, row, batch) or (row, k, batch) after its unit stride
@@ -658,8 +715,8 @@ __device__ __forceinline__ void tc_tile(const TcGemmArgs& g, const int m0, const
             bulk_copy(dst0 + s * STAGE, base + (long long)c * (blk / 4), blk, &txb[s]);
             if (tma) {
                 unsigned char* rdst = tsm_raw + s * STAGE + RAW;
-                if (lmode == MVEC) tma_load3(rdst, g.tmap, lr0, c * BK, lz, &txb[s]);
-                else tma_load3(rdst, g.tmap, c * BK, lr0, lz, &txb[s]);
+                if (lmode == MVEC) tma_load3(rdst, g.tmap, lr0, (kc0 + c) * BK, lz, &txb[s]);
+                else tma_load3(rdst, g.tmap, (kc0 + c) * BK, lr0, lz, &txb[s]);
             }
             issued = c + 1;
         }
@@ -680,7 +737,9 @@ __device__ __forceinline__ void tc_tile(const TcGemmArgs& g, const int m0, const
 
 template <int BN, int PRE>
 __global__ void __launch_bounds__(tc::kThreads, 1) tc_gemm_kernel(const TcGemmArgs g) {
-    tc_tile<BN, PRE>(g, blockIdx.x * tc::BM, blockIdx.y * BN, blockIdx.z);
+    const int z = (int)blockIdx.z;
+    const int s = g.splits > 1 ? z / g.batch : 0;   // z = s * batch + b
+    tc_tile<BN, PRE, true>(g, blockIdx.x * tc::BM, blockIdx.y * BN, z - s * g.batch, s);
 }
 
 // Grouped form: independent GEMMs of different shapes in one launch; CTA i
@@ -688,7 +747,7 @@ __global__ void __launch_bounds__(tc::kThreads, 1) tc_gemm_kernel(const TcGemmAr
 template <int BN, int PRE>
 __global__ void __launch_bounds__(tc::kThreads, 1) tc_gemm_grouped_kernel(const TcGemmArgs* gs, const int4* items) {
     const int4 it = items[blockIdx.x];
-    tc_tile<BN, PRE>(gs[it.x], it.y * tc::BM, it.z * BN, it.w);
+    tc_tile<BN, PRE, false>(gs[it.x], it.y * tc::BM, it.z * BN, it.w, 0);
 }
 
 // Pre-split form of a rows x K operand X(r, k) = X[r * sR + k * sK] with
@@ -815,6 +874,104 @@ inline int tc_pick_width(const TcGemmArgs* gs, int count, int sms) {
     return best;
 }
 
+// A split of K for one launch: tile width, number of splits and the chunk
+// boundaries kb[0] = 0 < kb[1] < ... < kb[splits] = ceil(K / 32).
+struct TcPlan {
+    int bn = 64;
+    int splits = 1;
+    int kb[5] = {0, 0, 0, 0, 0};
+};
+
+// Start-up and end of a CTA (barrier and tensor-memory set-up, filling the
+// pipeline, draining the last chunk groups, storing the tile), and the extra
+// end of a CTA of a split product (its partial tile out, the partials in),
+// in K chunks of pipeline time: a CTA's first MMA comes about two chunk
+// intervals after it starts.
+constexpr double kTcBlockOverhead = 3.0, kTcSplitOverhead = 0.75;
+
+// Estimated time of `tiles` tiles whose K chunks are split at kb: the CTAs
+// start in launch order (every tile of split 0, then of split 1, ...), each on
+// the first SM to free up, and a CTA costs its chunks plus the overheads.
+inline double tc_makespan(long long tiles, int splits, const int* kb, double per_chunk, int sms) {
+    const double extra = kTcBlockOverhead + (splits > 1 ? kTcSplitOverhead : 0.0);
+    if (splits == 1) return (double)((tiles + sms - 1) / sms) * per_chunk * (kb[1] + extra);
+    std::priority_queue<double, std::vector<double>, std::greater<double>> free_at;
+    const long long n = std::min<long long>(sms, tiles * splits);
+    for (long long i = 0; i < n; ++i) free_at.push(0.0);
+    double end = 0.0;
+    for (int sp = 0; sp < splits; ++sp) {
+        const double cost = per_chunk * ((kb[sp + 1] - kb[sp]) + extra);
+        for (long long t = 0; t < tiles; ++t) {
+            const double t0 = free_at.top();
+            free_at.pop();
+            free_at.push(t0 + cost);
+            end = std::max(end, t0 + cost);
+        }
+    }
+    return end;
+}
+
+// Fastest estimated tile width and split of K for one GEMM on `sms` SMs
+// (bn fixed when a pre-split B operand was tiled for it; splits only with
+// allow_split: the caller then provides the workspace and counters).  A
+// split is taken only when it is estimated 5% faster than none.
+inline TcPlan tc_plan(const TcGemmArgs& g, int sms, int fixed_bn, bool allow_split) {
+    const int nkc = (g.K + tc::BK - 1) / tc::BK;
+    TcPlan best;
+    double best_t = 1e300;
+    for (int bn : kTcWidths) {
+        if (fixed_bn && bn != fixed_bn) continue;
+        const long long tiles = tc_tiles(g, bn);
+        const double per_chunk = tc_cost(1, bn, 1, 1);
+        // candidate boundaries: no split; two parts (the first the larger, so
+        // that the second parts fill the SMs the first leaves idle); three
+        // and four equal parts
+        std::vector<std::vector<int>> cands;
+        cands.push_back({0, nkc});
+        if (allow_split && tiles < 2LL * sms) {
+            for (int f : {50, 60, 67, 75, 80}) {
+                const int c1 = (nkc * f + 50) / 100;
+                if (c1 >= 1 && c1 < nkc) cands.push_back({0, c1, nkc});
+            }
+            for (int S = 3; S <= kTcMaxSplits; ++S) {
+                if (nkc < 2 * S) break;
+                std::vector<int> kb(S + 1);
+                for (int i = 0; i <= S; ++i) kb[i] = (int)((long long)nkc * i / S);
+                cands.push_back(kb);
+            }
+        }
+        for (const std::vector<int>& kb : cands) {
+            const int S = (int)kb.size() - 1;
+            const double t = tc_makespan(tiles, S, kb.data(), per_chunk, sms) * (S > 1 ? 1.05 : 1.0);
+            if (t < best_t * 0.999) {
+                best_t = t;
+                best.bn = bn;
+                best.splits = S;
+                for (int i = 0; i < 5; ++i) best.kb[i] = i <= S ? kb[i] : nkc;
+            }
+        }
+    }
+    return best;
+}
+
+// Floats of the workspace and counters of a split plan for GEMM g.
+inline long long tc_split_ws_floats(const TcGemmArgs& g, const TcPlan& p) {
+    return p.splits > 1 ? (long long)p.splits * tc_tiles(g, p.bn) * tc::BM * p.bn : 0;
+}
+inline long long tc_split_counters(const TcGemmArgs& g, const TcPlan& p) {
+    return p.splits > 1 ? tc_tiles(g, p.bn) : 0;
+}
+
+// Sets g's tile width and split from plan p (workspace ws and zeroed
+// counters cnt sized by tc_split_ws_floats and tc_split_counters).
+inline void tc_apply_plan(TcGemmArgs& g, const TcPlan& p, float* ws, unsigned* cnt) {
+    g.bn = p.bn;
+    g.splits = p.splits > 1 ? p.splits : 0;
+    for (int i = 0; i < 5; ++i) g.kb[i] = p.kb[i];
+    g.ws = p.splits > 1 ? ws : nullptr;
+    g.cnt = p.splits > 1 ? cnt : nullptr;
+}
+
 inline int tc_sm_count() {
     static int sms = 0;
     if (!sms) {
@@ -830,7 +987,8 @@ template <int BN, int PRE>
 inline cudaError_t launch_tc_gemm_w(const TcGemmArgs& g, cudaStream_t st) {
     const size_t sm = tc_smem_bytes<BN, PRE>();
     cudaFuncSetAttribute(tc_gemm_kernel<BN, PRE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    const dim3 grid((unsigned)((g.M + tc::BM - 1) / tc::BM), (unsigned)((g.N + BN - 1) / BN), (unsigned)g.batch);
+    const unsigned zs = (unsigned)(g.splits > 1 ? g.splits : 1);
+    const dim3 grid((unsigned)((g.M + tc::BM - 1) / tc::BM), (unsigned)((g.N + BN - 1) / BN), (unsigned)g.batch * zs);
     tc_gemm_kernel<BN, PRE><<<grid, tc::kThreads, sm, st>>>(g);
     return cudaGetLastError();
 }
@@ -850,6 +1008,16 @@ inline cudaError_t launch_tc_gemm_p(const TcGemmArgs& g, int bn, cudaStream_t st
 inline cudaError_t launch_tc_gemm(const TcGemmArgs& g, cudaStream_t st) {
     if (g.M <= 0 || g.N <= 0 || g.K <= 0 || g.batch <= 0 || g.pre < 0 || g.pre > 2) return cudaErrorInvalidValue;
     if (g.pre == 2 && g.bn == 0) return cudaErrorInvalidValue;
+    if (g.splits > 1) {
+        // a split needs its width fixed (the workspace is sized for it), the
+        // workspace and counters, and non-empty chunk ranges covering K
+        const int nkc = (g.K + tc::BK - 1) / tc::BK;
+        if (g.splits > kTcMaxSplits || g.bn == 0 || !g.ws || !g.cnt || g.kb[0] != 0 || g.kb[g.splits] != nkc ||
+            (long long)g.batch * g.splits > 65535)
+            return cudaErrorInvalidValue;
+        for (int i = 0; i < g.splits; ++i)
+            if (g.kb[i + 1] <= g.kb[i]) return cudaErrorInvalidValue;
+    }
     const int bn = g.bn ? g.bn : tc_pick_width(&g, 1, tc_sm_count());
     if (g.pre == 1) return launch_tc_gemm_p<1>(g, bn, st);
     if (g.pre == 2) return launch_tc_gemm_p<2>(g, bn, st);

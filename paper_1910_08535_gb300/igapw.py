@@ -66,7 +66,7 @@ _SIGS = {
     'igapw_batch_create': (_I, [ctypes.POINTER(_VP), ctypes.POINTER(igapw_desc), _I, _VP]),
     'igapw_batch_source_sine': (_I, [_VP, ctypes.POINTER(_D)]),
     'igapw_batch_solve': (_I, [_VP]),
-    'igapw_tc_gemm': (_I, [_I, _I, _I, _I, _VP, _LL, _LL, _LL, _VP, _LL, _LL, _LL, _VP, _LL, _LL, _LL, _I, _I, _VP]),
+    'igapw_tc_gemm': (_I, [_I, _I, _I, _I, _VP, _LL, _LL, _LL, _VP, _LL, _LL, _LL, _VP, _LL, _LL, _LL, _I, _I, _I, _VP]),
     'igapw_batch_sync_status': (_I, [_VP]),
     'igapw_batch_tensor': (_I, [_VP, _I, _I, ctypes.POINTER(_VP), ctypes.POINTER(ctypes.c_longlong)]),
     'igapw_batch_info': (_I, [_VP, ctypes.POINTER(_I)]),
@@ -245,18 +245,19 @@ def igapw_destroy(ctx):
     _check(load().igapw_destroy(ctx), None)
 
 
-def igapw_tc_gemm(M, N, K, batch, A, sA, bA, B, sB, bB, D, sD, bD, pre=0, bn=0, stream=None):
+def igapw_tc_gemm(M, N, K, batch, A, sA, bA, B, sB, bB, D, sD, bD, pre=0, bn=0, splits=0, stream=None):
     """The library's tensor-core transform GEMM on device pointers:
     D(m, n) = sum_k A(m, k) B(n, k) per batch entry; sA = (s_m, s_k),
     sB = (s_n, s_k), sD = (s_m, s_n) element strides.  Synchronous."""
     _check(load().igapw_tc_gemm(M, N, K, batch, A, sA[0], sA[1], bA, B, sB[0], sB[1], bB, D, sD[0], sD[1], bD, pre, bn,
-                                _stream_handle(stream)), None)
+                                splits, _stream_handle(stream)), None)
 
 
-def tc_gemm(a, b, out=None, pre=0, bn=0):
+def tc_gemm(a, b, out=None, pre=0, bn=0, splits=0):
     """Torch convenience form: D = A @ B^T for CUDA float32 tensors A (M x K)
     and B (N x K) of any strides (or batched, (batch, M, K) and (batch, N, K),
-    a pre-split operand shared by the batch as a 2D tensor)."""
+    a pre-split operand shared by the batch as a 2D tensor).  bn: tile width
+    (0: chosen); splits: K split over CTAs (0: chosen, 1: none, 2-4)."""
     import torch
     if a.dtype != torch.float32 or b.dtype != torch.float32 or not (a.is_cuda and b.is_cuda):
         raise IgapwError(IGAPW_ERR_ARG, 'tc_gemm: CUDA float32 tensors required')
@@ -275,7 +276,7 @@ def tc_gemm(a, b, out=None, pre=0, bn=0):
     bB = sb[0] if b.dim() == 3 else 0
     bD = so[0] if out.dim() == 3 else 0
     igapw_tc_gemm(M, N, K, batch, a.data_ptr(), sa[-2:], bA, b.data_ptr(), sb[-2:], bB, out.data_ptr(), so[-2:], bD,
-                  pre, bn, torch.cuda.current_stream())
+                  pre, bn, splits, torch.cuda.current_stream())
     return out
 
 

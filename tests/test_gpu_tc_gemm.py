@@ -2,7 +2,8 @@
 (igapw_tc_gemm) element by element against the FP64 product of the same FP32
 operands: every combination of operand layout (unit stride along K, along
 the rows, neither), pre-split operand, tile width, batch and ragged edges
-(sizes that are not multiples of the 128 x bn x 32 tiles), and the
+(sizes that are not multiples of the 128 x bn x 32 tiles), K split over
+several CTAs per tile (partials added by the tile's last CTA), and the
 1032 x 1027 x 1032 shape of the 1024^2 Poisson transforms.
 
 Bound per element: |D - A B^T| <= (2^-20 + K 2^-23) (|A| |B|^T), twice the
@@ -80,24 +81,67 @@ def test_layouts_and_presplit(M, N, K, batch, la, lb, pre):
 
 @pytest.mark.parametrize('bn', [64, 96, 128])
 @pytest.mark.parametrize('pre', [0, 1, 2])
-def test_tile_widths(bn, pre):
+@pytest.mark.parametrize('splits', [1, 3])
+def test_tile_widths(bn, pre, splits):
     from paper_1910_08535_gb300 import igapw
     rng = np.random.Generator(np.random.PCG64(bn + pre))
     a, ta = _operand(rng, 300, 100, 'm', 1)
     b, tb = _operand(rng, 270, 100, 'k', 1)
-    d = igapw.tc_gemm(ta[0], tb[0], pre=pre, bn=bn)
+    d = igapw.tc_gemm(ta[0], tb[0], pre=pre, bn=bn, splits=splits)
     _check(a, b, d.cpu().numpy()[None])
 
 
+@pytest.mark.parametrize('splits', [2, 3, 4])
+@pytest.mark.parametrize('pre,la,lb', [(0, 'k', 'm'), (1, 'm', 'k'), (2, 'm', 'm'), (1, 'x', 'x')])
+def test_split_k(splits, pre, la, lb):
+    """K = 200 (7 chunks, the last ragged) split into 2-4 ranges of chunks
+    over a batch of 2 with ragged tiles in M and N; the same call twice gives
+    bit-identical results (the partials are added in split order whichever
+    CTA finishes last)."""
+    import torch
+    from paper_1910_08535_gb300 import igapw
+    rng = np.random.Generator(np.random.PCG64(100 * splits + 10 * pre + len(la)))
+    batch, M, N, K = 2, 300, 170, 200
+    a, ta = _operand(rng, M, K, la, batch)
+    b, tb = _operand(rng, N, K, lb, batch)
+    if pre == 1:
+        a = np.repeat(a[:1], batch, axis=0)
+        ta = ta[0]
+    if pre == 2:
+        b = np.repeat(b[:1], batch, axis=0)
+        tb = tb[0]
+    d1 = igapw.tc_gemm(ta, tb, pre=pre, bn=64, splits=splits)
+    d2 = igapw.tc_gemm(ta, tb, pre=pre, bn=64, splits=splits)
+    torch.cuda.synchronize()
+    assert torch.equal(d1, d2)
+    _check(a, b, d1.cpu().numpy().reshape(batch, M, N))
+
+
+def test_split_matches_unsplit_within_rounding():
+    """Splitting K changes only the order of the FP32 additions of the chunk
+    sums: the split and unsplit results agree to a few ulps of the terms."""
+    from paper_1910_08535_gb300 import igapw
+    rng = np.random.Generator(np.random.PCG64(77))
+    a, ta = _operand(rng, 260, 1000, 'k', 1)
+    b, tb = _operand(rng, 190, 1000, 'k', 1)
+    d1 = igapw.tc_gemm(ta[0], tb[0], pre=1, bn=96, splits=1).cpu().numpy().astype(np.float64)
+    d4 = igapw.tc_gemm(ta[0], tb[0], pre=1, bn=96, splits=4).cpu().numpy().astype(np.float64)
+    bound = np.abs(a[0]).astype(np.float64) @ np.abs(b[0]).astype(np.float64).T
+    assert np.max(np.abs(d1 - d4) / bound) < 64 * 2.0 ** -24
+    _check(a, b, d4[None].astype(np.float32))
+
+
 @pytest.mark.parametrize('pre,la,lb', [(1, 'm', 'k'), (2, 'm', 'm'), (0, 'k', 'k')])
-def test_poisson_transform_shape(pre, la, lb):
+@pytest.mark.parametrize('splits', [0, 1])
+def test_poisson_transform_shape(pre, la, lb, splits):
     """1032 x 1027 x 1032: the x and y transforms of the 1024^2 p = 3 solve
-    (the matrix operand pre-split, the data operand live)."""
+    (the matrix operand pre-split, the data operand live), with the split of
+    K the cost model picks for 99 tiles on the GPU's SMs and without."""
     from paper_1910_08535_gb300 import igapw
     rng = np.random.Generator(np.random.PCG64(11 + pre))
     a, ta = _operand(rng, 1032, 1032, la, 1)
     b, tb = _operand(rng, 1027, 1032, lb, 1)
-    d = igapw.tc_gemm(ta[0], tb[0], pre=pre)
+    d = igapw.tc_gemm(ta[0], tb[0], pre=pre, splits=splits)
     _check(a, b, d.cpu().numpy()[None])
 
 
@@ -113,4 +157,12 @@ def test_rejects_bad_arguments():
     y = torch.zeros((2, 4, 4), dtype=torch.float32, device='cuda')
     with pytest.raises(igapw.IgapwError) as e:
         igapw.tc_gemm(y, y, pre=1)   # pre-split operand with a batch stride
+    assert e.value.code == igapw.IGAPW_ERR_ARG
+    z = torch.zeros((4, 100), dtype=torch.float32, device='cuda')
+    for splits in (-1, 5):   # outside 0 .. 4
+        with pytest.raises(igapw.IgapwError) as e:
+            igapw.tc_gemm(z, z, splits=splits)
+        assert e.value.code == igapw.IGAPW_ERR_ARG
+    with pytest.raises(igapw.IgapwError) as e:
+        igapw.tc_gemm(x, x, splits=2)   # K = 4: one chunk of 32, nothing to split
     assert e.value.code == igapw.IGAPW_ERR_ARG
