@@ -158,6 +158,142 @@ inline long long tc_presplit_floats(int rows, int K, int R, bool comb) {
     return (long long)((rows + R - 1) / R) * ((K + tc::BK - 1) / tc::BK) * (tc_presplit_block_bytes(R, comb) / 4);
 }
 
+// ---- launch planning (host code) ----------------------------------------------
+// Tile widths the kernels are built for (multiples of 32: the loaders read
+// 16 columns per tensor-memory load, per half of the warps; at most 128: the
+// four accumulator halves fill the 512 tensor-memory columns of an SM).
+constexpr int kTcWidths[3] = {64, 96, 128};
+
+// Estimated time (arbitrary units) of tiles of width bn over `sms` SMs: the
+// split-TF32 MMAs with N <= 256 are bound by shared-memory bandwidth (about
+// 128 bytes per clock on an SM), so a K chunk of one tile costs its shared
+// traffic: per K step the two MMAs read A_hi and A_lo (BM x 8 each) and B
+// (2 bn x 8 and bn x 8) 4-byte values, and the hi and lo parts of both
+// operands are written once.  Tiles are
+// spread over the SMs, so the busiest SM holds ceil(tiles / sms) of them.
+inline double tc_cost(long long tiles, int bn, long long chunks, int sms) {
+    const double per_chunk = (4.0 * (2 * tc::BM + 3 * bn) * 8 * 4 + 2.0 * (tc::BM + bn) * tc::BK * 4) / 128.0;
+    return (double)((tiles + sms - 1) / sms) * per_chunk * (double)chunks;
+}
+
+inline long long tc_tiles(const TcGemmArgs& g, int bn) {
+    return (long long)((g.M + tc::BM - 1) / tc::BM) * ((g.N + bn - 1) / bn) * g.batch;
+}
+
+// Tile width of the fastest estimated cover of a set of GEMMs (one launch).
+inline int tc_pick_width(const TcGemmArgs* gs, int count, int sms) {
+    int best = 64;
+    double best_t = 1e300;
+    for (int bn : kTcWidths) {
+        long long tiles = 0, chunks = 0;
+        for (int i = 0; i < count; ++i) {
+            tiles += tc_tiles(gs[i], bn);
+            chunks = std::max<long long>(chunks, (gs[i].K + tc::BK - 1) / tc::BK);
+        }
+        const double t = tc_cost(tiles, bn, chunks, sms);
+        if (t < best_t * 0.999) { best_t = t; best = bn; }
+    }
+    return best;
+}
+
+// A split of K for one launch: tile width, number of splits and the chunk
+// boundaries kb[0] = 0 < kb[1] < ... < kb[splits] = ceil(K / 32).
+struct TcPlan {
+    int bn = 64;
+    int splits = 1;
+    int kb[5] = {0, 0, 0, 0, 0};
+};
+
+// Start-up and end of a CTA (barrier and tensor-memory set-up, filling the
+// pipeline, draining the last chunk groups, storing the tile), and the extra
+// end of a CTA of a split product (its partial tile out, the partials in),
+// in K chunks of pipeline time: a CTA's first MMA comes about two chunk
+// intervals after it starts.
+constexpr double kTcBlockOverhead = 3.0, kTcSplitOverhead = 0.75;
+
+// Estimated time of `tiles` tiles whose K chunks are split at kb: the CTAs
+// start in launch order (every tile of split 0, then of split 1, ...), each on
+// the first SM to free up, and a CTA costs its chunks plus the overheads.
+inline double tc_makespan(long long tiles, int splits, const int* kb, double per_chunk, int sms) {
+    const double extra = kTcBlockOverhead + (splits > 1 ? kTcSplitOverhead : 0.0);
+    if (splits == 1) return (double)((tiles + sms - 1) / sms) * per_chunk * (kb[1] + extra);
+    std::priority_queue<double, std::vector<double>, std::greater<double>> free_at;
+    const long long n = std::min<long long>(sms, tiles * splits);
+    for (long long i = 0; i < n; ++i) free_at.push(0.0);
+    double end = 0.0;
+    for (int sp = 0; sp < splits; ++sp) {
+        const double cost = per_chunk * ((kb[sp + 1] - kb[sp]) + extra);
+        for (long long t = 0; t < tiles; ++t) {
+            const double t0 = free_at.top();
+            free_at.pop();
+            free_at.push(t0 + cost);
+            end = std::max(end, t0 + cost);
+        }
+    }
+    return end;
+}
+
+// Fastest estimated tile width and split of K for one GEMM on `sms` SMs
+// (bn fixed when a pre-split B operand was tiled for it; splits only with
+// allow_split: the caller then provides the workspace and counters).  A
+// split is taken only when it is estimated 5% faster than none.
+inline TcPlan tc_plan(const TcGemmArgs& g, int sms, int fixed_bn, bool allow_split) {
+    const int nkc = (g.K + tc::BK - 1) / tc::BK;
+    TcPlan best;
+    double best_t = 1e300;
+    for (int bn : kTcWidths) {
+        if (fixed_bn && bn != fixed_bn) continue;
+        const long long tiles = tc_tiles(g, bn);
+        const double per_chunk = tc_cost(1, bn, 1, 1);
+        // candidate boundaries: no split; two parts (the first the larger, so
+        // that the second parts fill the SMs the first leaves idle); three
+        // and four equal parts
+        std::vector<std::vector<int>> cands;
+        cands.push_back({0, nkc});
+        if (allow_split && tiles < 2LL * sms) {
+            for (int f : {50, 60, 67, 75, 80}) {
+                const int c1 = (nkc * f + 50) / 100;
+                if (c1 >= 1 && c1 < nkc) cands.push_back({0, c1, nkc});
+            }
+            for (int S = 3; S <= kTcMaxSplits; ++S) {
+                if (nkc < 2 * S) break;
+                std::vector<int> kb(S + 1);
+                for (int i = 0; i <= S; ++i) kb[i] = (int)((long long)nkc * i / S);
+                cands.push_back(kb);
+            }
+        }
+        for (const std::vector<int>& kb : cands) {
+            const int S = (int)kb.size() - 1;
+            const double t = tc_makespan(tiles, S, kb.data(), per_chunk, sms) * (S > 1 ? 1.05 : 1.0);
+            if (t < best_t * 0.999) {
+                best_t = t;
+                best.bn = bn;
+                best.splits = S;
+                for (int i = 0; i < 5; ++i) best.kb[i] = i <= S ? kb[i] : nkc;
+            }
+        }
+    }
+    return best;
+}
+
+// Floats of the workspace and counters of a split plan for GEMM g.
+inline long long tc_split_ws_floats(const TcGemmArgs& g, const TcPlan& p) {
+    return p.splits > 1 ? (long long)p.splits * tc_tiles(g, p.bn) * tc::BM * p.bn : 0;
+}
+inline long long tc_split_counters(const TcGemmArgs& g, const TcPlan& p) {
+    return p.splits > 1 ? tc_tiles(g, p.bn) : 0;
+}
+
+// Sets g's tile width and split from plan p (workspace ws and zeroed
+// counters cnt sized by tc_split_ws_floats and tc_split_counters).
+inline void tc_apply_plan(TcGemmArgs& g, const TcPlan& p, float* ws, unsigned* cnt) {
+    g.bn = p.bn;
+    g.splits = p.splits > 1 ? p.splits : 0;
+    for (int i = 0; i < 5; ++i) g.kb[i] = p.kb[i];
+    g.ws = p.splits > 1 ? ws : nullptr;
+    g.cnt = p.splits > 1 ? cnt : nullptr;
+}
+
 #ifndef IGAPW_HOST_EMU
 namespace tc {
 
@@ -835,141 +971,6 @@ inline bool tc_make_tmap(CUtensorMap* m, const float* X, long long sR, long long
     return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(X), dims, strides, box, es,
                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
-}
-
-// Tile widths the kernels are built for (multiples of 32: the loaders read
-// 16 columns per tensor-memory load, per half of the warps; at most 128: the
-// four accumulator halves fill the 512 tensor-memory columns of an SM).
-constexpr int kTcWidths[3] = {64, 96, 128};
-
-// Estimated time (arbitrary units) of tiles of width bn over `sms` SMs: the
-// split-TF32 MMAs with N <= 256 are bound by shared-memory bandwidth (about
-// 128 bytes per clock on an SM), so a K chunk of one tile costs its shared
-// traffic: per K step the two MMAs read A_hi and A_lo (BM x 8 each) and B
-// (2 bn x 8 and bn x 8) 4-byte values, and the hi and lo parts of both
-// operands are written once.  Tiles are
-// spread over the SMs, so the busiest SM holds ceil(tiles / sms) of them.
-inline double tc_cost(long long tiles, int bn, long long chunks, int sms) {
-    const double per_chunk = (4.0 * (2 * tc::BM + 3 * bn) * 8 * 4 + 2.0 * (tc::BM + bn) * tc::BK * 4) / 128.0;
-    return (double)((tiles + sms - 1) / sms) * per_chunk * (double)chunks;
-}
-
-inline long long tc_tiles(const TcGemmArgs& g, int bn) {
-    return (long long)((g.M + tc::BM - 1) / tc::BM) * ((g.N + bn - 1) / bn) * g.batch;
-}
-
-// Tile width of the fastest estimated cover of a set of GEMMs (one launch).
-inline int tc_pick_width(const TcGemmArgs* gs, int count, int sms) {
-    int best = 64;
-    double best_t = 1e300;
-    for (int bn : kTcWidths) {
-        long long tiles = 0, chunks = 0;
-        for (int i = 0; i < count; ++i) {
-            tiles += tc_tiles(gs[i], bn);
-            chunks = std::max<long long>(chunks, (gs[i].K + tc::BK - 1) / tc::BK);
-        }
-        const double t = tc_cost(tiles, bn, chunks, sms);
-        if (t < best_t * 0.999) { best_t = t; best = bn; }
-    }
-    return best;
-}
-
-// A split of K for one launch: tile width, number of splits and the chunk
-// boundaries kb[0] = 0 < kb[1] < ... < kb[splits] = ceil(K / 32).
-struct TcPlan {
-    int bn = 64;
-    int splits = 1;
-    int kb[5] = {0, 0, 0, 0, 0};
-};
-
-// Start-up and end of a CTA (barrier and tensor-memory set-up, filling the
-// pipeline, draining the last chunk groups, storing the tile), and the extra
-// end of a CTA of a split product (its partial tile out, the partials in),
-// in K chunks of pipeline time: a CTA's first MMA comes about two chunk
-// intervals after it starts.
-constexpr double kTcBlockOverhead = 3.0, kTcSplitOverhead = 0.75;
-
-// Estimated time of `tiles` tiles whose K chunks are split at kb: the CTAs
-// start in launch order (every tile of split 0, then of split 1, ...), each on
-// the first SM to free up, and a CTA costs its chunks plus the overheads.
-inline double tc_makespan(long long tiles, int splits, const int* kb, double per_chunk, int sms) {
-    const double extra = kTcBlockOverhead + (splits > 1 ? kTcSplitOverhead : 0.0);
-    if (splits == 1) return (double)((tiles + sms - 1) / sms) * per_chunk * (kb[1] + extra);
-    std::priority_queue<double, std::vector<double>, std::greater<double>> free_at;
-    const long long n = std::min<long long>(sms, tiles * splits);
-    for (long long i = 0; i < n; ++i) free_at.push(0.0);
-    double end = 0.0;
-    for (int sp = 0; sp < splits; ++sp) {
-        const double cost = per_chunk * ((kb[sp + 1] - kb[sp]) + extra);
-        for (long long t = 0; t < tiles; ++t) {
-            const double t0 = free_at.top();
-            free_at.pop();
-            free_at.push(t0 + cost);
-            end = std::max(end, t0 + cost);
-        }
-    }
-    return end;
-}
-
-// Fastest estimated tile width and split of K for one GEMM on `sms` SMs
-// (bn fixed when a pre-split B operand was tiled for it; splits only with
-// allow_split: the caller then provides the workspace and counters).  A
-// split is taken only when it is estimated 5% faster than none.
-inline TcPlan tc_plan(const TcGemmArgs& g, int sms, int fixed_bn, bool allow_split) {
-    const int nkc = (g.K + tc::BK - 1) / tc::BK;
-    TcPlan best;
-    double best_t = 1e300;
-    for (int bn : kTcWidths) {
-        if (fixed_bn && bn != fixed_bn) continue;
-        const long long tiles = tc_tiles(g, bn);
-        const double per_chunk = tc_cost(1, bn, 1, 1);
-        // candidate boundaries: no split; two parts (the first the larger, so
-        // that the second parts fill the SMs the first leaves idle); three
-        // and four equal parts
-        std::vector<std::vector<int>> cands;
-        cands.push_back({0, nkc});
-        if (allow_split && tiles < 2LL * sms) {
-            for (int f : {50, 60, 67, 75, 80}) {
-                const int c1 = (nkc * f + 50) / 100;
-                if (c1 >= 1 && c1 < nkc) cands.push_back({0, c1, nkc});
-            }
-            for (int S = 3; S <= kTcMaxSplits; ++S) {
-                if (nkc < 2 * S) break;
-                std::vector<int> kb(S + 1);
-                for (int i = 0; i <= S; ++i) kb[i] = (int)((long long)nkc * i / S);
-                cands.push_back(kb);
-            }
-        }
-        for (const std::vector<int>& kb : cands) {
-            const int S = (int)kb.size() - 1;
-            const double t = tc_makespan(tiles, S, kb.data(), per_chunk, sms) * (S > 1 ? 1.05 : 1.0);
-            if (t < best_t * 0.999) {
-                best_t = t;
-                best.bn = bn;
-                best.splits = S;
-                for (int i = 0; i < 5; ++i) best.kb[i] = i <= S ? kb[i] : nkc;
-            }
-        }
-    }
-    return best;
-}
-
-// Floats of the workspace and counters of a split plan for GEMM g.
-inline long long tc_split_ws_floats(const TcGemmArgs& g, const TcPlan& p) {
-    return p.splits > 1 ? (long long)p.splits * tc_tiles(g, p.bn) * tc::BM * p.bn : 0;
-}
-inline long long tc_split_counters(const TcGemmArgs& g, const TcPlan& p) {
-    return p.splits > 1 ? tc_tiles(g, p.bn) : 0;
-}
-
-// Sets g's tile width and split from plan p (workspace ws and zeroed
-// counters cnt sized by tc_split_ws_floats and tc_split_counters).
-inline void tc_apply_plan(TcGemmArgs& g, const TcPlan& p, float* ws, unsigned* cnt) {
-    g.bn = p.bn;
-    g.splits = p.splits > 1 ? p.splits : 0;
-    for (int i = 0; i < 5; ++i) g.kb[i] = p.kb[i];
-    g.ws = p.splits > 1 ? ws : nullptr;
-    g.cnt = p.splits > 1 ? cnt : nullptr;
 }
 
 inline int tc_sm_count() {
