@@ -24,7 +24,9 @@
 //     matrices) can be split once, ahead of time, into exactly that layout
 //     (tc_presplit); warp 9 then streams its chunks with bulk asynchronous
 //     copies (cp.async.bulk) that complete on a per-stage mbarrier, and the
-//     loaders handle the other operand only;
+//     loaders handle the other operand only; given a tensor map of that live
+//     operand, warp 9 also brings its raw FP32 chunk into the stage by TMA
+//     (cp.async.bulk.tensor) and the loaders split it from shared memory;
 //   - warp 8 waits until the stage is complete (the loaders' `full` barrier
 //     and the copy's), issues the chunk's 8 MMAs (4 K-steps, each
 //     A_hi [B_hi; B_lo] with N = 2 BN into adjacent accumulators and A_lo
@@ -35,6 +37,10 @@
 //   - the loaders add each group's partial sums (tcgen05.ld, one row per
 //     thread, half the columns per warp) into FP32 registers, which frees
 //     the buffer for the group after next, and finally store D.
+// When the tiles alone would leave SMs idle, the host plan (tc_plan) splits
+// the K chunks of every tile over up to 4 CTAs; each writes its partial tile
+// to a workspace and the last to finish adds them in split order (no CTA
+// waits on another).
 // Summing the groups in registers matters for accuracy: the tensor core
 // truncates when it accumulates (measured: a drift toward zero of about
 // 2^-25 per accumulation step), which over all of K would cost the solver's
