@@ -104,12 +104,17 @@ def base_state(shape):
 
 def slot_bytes(shape):
     """Resident device bytes of a slot (estimate): the context's tables and
-    scratch and the slot's tensors at 8 bytes per coefficient, plus the dense
-    1D transforms of a Poisson context."""
+    scratch and the slot's tensors at 8 bytes per coefficient, plus, for a
+    Poisson context, the dense 1D transforms (W and V per axis, FP32), their
+    hi/lo tiles for the tensor-core GEMM (two FP32 parts per value, tiles of
+    up to 128 rows and 32 columns, 1/8 layout gaps) and the GEMM's split-K
+    partial tiles and counters (under 10 MB on the 2D ladder's largest grid)."""
     n = shape.n_elem + shape.degree
     b = 6 * 8 * shape.ntot + (4 << 20)
     if shape.kind == 'poisson':
         b += shape.dim * 2 * 4 * n * n
+        b += shape.dim * 2 * 10 * (n + 128) * (n + 32)
+        b += 16 << 20
     return b
 
 

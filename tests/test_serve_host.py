@@ -43,6 +43,13 @@ def test_slot_bytes_grow_with_size_and_cover_tensors():
     # resident: tensors plus the dense 1D transforms; nothing transient (the
     # library evaluates the source into the slot's right-hand-side tensor)
     assert serve.slot_bytes(p) >= 8 * p.ntot + 3 * 2 * 4 * (p.n_elem + p.degree) ** 2
+    # ... and the transforms' hi/lo tiles for the tensor-core GEMM: per axis
+    # and matrix ceil(n / 128) x ceil(n / 32) blocks of 2 x 128 x 32 values
+    # (an A operand), each tile 8 x (128/8 x 144 + 16) bytes
+    n = p.n_elem + p.degree
+    blocks = -(-n // 128) * -(-n // 32)
+    tiles = 3 * 2 * blocks * 2 * 8 * (128 // 8 * 144 + 16)
+    assert serve.slot_bytes(p) >= 8 * p.ntot + 3 * 2 * 4 * n ** 2 + tiles
     assert serve.transient_bytes(p) == 0
     assert serve.transient_bytes(serve.Shape('poisson', 3, 160, 3, 'fp32r')) == 0
     # the largest request of the mixed stream fits the 120 GB budget several times over
